@@ -1,0 +1,137 @@
+/*
+ * CPU oracle for hashless content-defined chunking: RAM, AE-Max, AE-Min, MAXP.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the plain, slow, sequential
+ * statement of what the chunkers compute. Only the tests, the smoke check
+ * and the benchmark's CPU-baseline leg may load it. It shares no code,
+ * header, table or helper with the GPU library.
+ *
+ * Source: arxiv 2508.05797 ("VectorCDC"), Section 2.1 (the AE, MAXP and RAM
+ * paragraphs) and Section 3.3 ("Putting it together"). The paper checks that
+ * its vector versions produce chunks identical to the native algorithms
+ * (Section 5.2, "Vector-acceleration Impact"); the GPU path is held to the
+ * same standard against this file.
+ *
+ * Conventions (shared by all algorithms):
+ *   - Bytes are unsigned 0..255 (the paper compares bytes as hexadecimal
+ *     values, e.g. 0xE1 vs 0x21 in Section 3.1).
+ *   - A chunk is [s, e); next(s) returns e. The chunker emits
+ *     e_1 = next(0), e_2 = next(e_1), ..., the last one equal to len.
+ *   - min / max bound the chunk size: no cut before s + min, a forced cut at
+ *     s + max (the usual CDC rule of Section 2.1, hash-based paragraph). The
+ *     final chunk ends at len and may be shorter than min.
+ *
+ * Readings of passages the paper leaves open (each is listed in the design
+ * notes with its reason):
+ *   RAM  : the cut goes right after the first byte at or beyond the window
+ *          whose value is >= the window maximum (GEQ), and that byte belongs
+ *          to the chunk. If no more than w bytes remain, the rest is one chunk.
+ *   AE   : a new target needs a strictly greater byte (GT); a byte equal to
+ *          the target inside the window does not block the cut; the cut goes
+ *          right after the w-byte window that follows the target.
+ *   MAXP : a target is strictly greater than every byte within distance w on
+ *          both sides; both windows must lie inside [0, len); windows may
+ *          reach back into the previous chunk (positional test); the cut goes
+ *          right after the target.
+ */
+#include <stddef.h>
+#include <stdint.h>
+
+enum { OR_RAM = 0, OR_AE_MAX = 1, OR_MAXP = 2, OR_AE_MIN = 3 };
+
+static uint64_t umin(uint64_t a, uint64_t b) { return a < b ? a : b; }
+static uint64_t umax(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+/* RAM (Section 2.1 "RAM"; Section 3.3: an extreme byte search over the window
+ * followed by a GEQ range scan). */
+uint64_t oracle_next_ram(const uint8_t* B, uint64_t len, uint64_t s,
+                         uint32_t w, uint32_t mn, uint32_t mx) {
+    if (len - s <= w) return len;
+    /* Extreme Byte Search: maximum of the w-byte window at the chunk start. */
+    uint8_t M = 0;
+    for (uint64_t i = s; i < s + w; i++)
+        if (B[i] > M) M = B[i];
+    /* Range Scan (GEQ) from the first byte outside the window. */
+    uint64_t limit = umin(len, s + mx);
+    for (uint64_t j = umax(s + w, s + mn - 1); j < limit; j++)
+        if (B[j] >= M) return j + 1;
+    return limit;
+}
+
+/* AE (Section 2.1 "AE"; Section 3.3). dir = +1 for AE-Max, -1 for AE-Min.
+ * p is the current target (extreme so far); the cut is placed after the
+ * w-byte window that follows p once that window holds no byte beyond it. */
+uint64_t oracle_next_ae(const uint8_t* B, uint64_t len, uint64_t s,
+                        uint32_t w, uint32_t mn, uint32_t mx, int dir) {
+    uint64_t limit = umin(len, s + mx);
+    uint64_t p = s;
+    for (uint64_t i = s + 1; i < limit; i++) {
+        int beyond = dir > 0 ? (B[i] > B[p]) : (B[i] < B[p]);
+        if (beyond)
+            p = i;                                  /* new target */
+        else if (i - p >= w && i + 1 - s >= mn)
+            return i + 1;                           /* window after p is clear */
+    }
+    return limit;
+}
+
+/* MAXP local-maximum test (Section 2.1 "MAXP"): i is a target when both
+ * w-byte windows around it lie inside [0, len) and every byte in them is
+ * strictly smaller than B[i]. */
+int oracle_maxp_is_target(const uint8_t* B, uint64_t len, uint64_t i, uint32_t w) {
+    if (i < w || i + w >= len) return 0;
+    for (uint64_t k = 1; k <= w; k++) {
+        if (B[i - k] >= B[i]) return 0;
+        if (B[i + k] >= B[i]) return 0;
+    }
+    return 1;
+}
+
+/* MAXP (Section 2.1 "MAXP"; Section 3.3: range scans for a target, each
+ * followed by the two window searches). The cut goes right after the first
+ * target c with c + 1 - s >= min; none before s + max forces a cut there. */
+uint64_t oracle_next_maxp(const uint8_t* B, uint64_t len, uint64_t s,
+                          uint32_t w, uint32_t mn, uint32_t mx) {
+    uint64_t limit = umin(len, s + mx);
+    for (uint64_t c = s + mn - 1; c < limit; c++)
+        if (oracle_maxp_is_target(B, len, c, w)) return c + 1;
+    return limit;
+}
+
+uint64_t oracle_next(int alg, const uint8_t* B, uint64_t len, uint64_t s,
+                     uint32_t w, uint32_t mn, uint32_t mx) {
+    switch (alg) {
+    case OR_RAM:    return oracle_next_ram(B, len, s, w, mn, mx);
+    case OR_AE_MAX: return oracle_next_ae(B, len, s, w, mn, mx, +1);
+    case OR_AE_MIN: return oracle_next_ae(B, len, s, w, mn, mx, -1);
+    case OR_MAXP:   return oracle_next_maxp(B, len, s, w, mn, mx);
+    default:        return 0;
+    }
+}
+
+/* Chunk the whole buffer from offset 0. Writes up to cap chunk ends (the
+ * boundaries) to out and returns how many there are in total. */
+uint64_t oracle_chunk(int alg, const uint8_t* B, uint64_t len,
+                      uint32_t w, uint32_t mn, uint32_t mx,
+                      uint64_t* out, uint64_t cap) {
+    uint64_t s = 0, n = 0;
+    while (s < len) {
+        uint64_t e = oracle_next(alg, B, len, s, w, mn, mx);
+        if (n < cap) out[n] = e;
+        n++;
+        s = e;
+    }
+    return n;
+}
+
+/* All MAXP targets in [0, len), in increasing order (up to cap written). */
+uint64_t oracle_maxp_targets(const uint8_t* B, uint64_t len, uint32_t w,
+                             uint64_t* out, uint64_t cap) {
+    uint64_t n = 0;
+    for (uint64_t i = 0; i < len; i++)
+        if (oracle_maxp_is_target(B, len, i, w)) {
+            if (n < cap) out[n] = i;
+            n++;
+        }
+    return n;
+}
