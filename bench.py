@@ -1,0 +1,347 @@
+"""Benchmark: chunking throughput of RAM, AE and MAXP on a 4 GiB mixed stream.
+
+One step = the whole hot path over one batch of input: the 4 GiB mixed
+stream (seed 1; 1 MiB blocks of uniform / text-like / zero-run bytes) chunked
+with RAM, AE and MAXP at mean chunk sizes 4, 8 and 16 KiB (min = mean/4,
+max = 8*mean, windows from the calibrated table) -- 9 library calls, inputs
+resident in HBM. value = bytes chunked / device time (GB/s, 1e9).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun), every rank chunks its own 4 GiB stream (seed 1 + rank):
+independent replicas, no data-path collective (weak scaling).
+The reference arm (--impl reference) times the CPU oracle on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GIB = 1 << 30
+MIB = 1 << 20
+STREAM_LEN = 4 * GIB
+ALGS = ("ram", "ae", "maxp")
+MEANS = (4096, 8192, 16384)
+METRIC = "chunking GB/s per algo (RAM/AE/MAXP), % of HBM peak; batched GB/s; p50/p99 lat"
+WORKLOAD = ("mixed stream 4 GiB (seed 1: 50% uniform, 30% Zipf-1.1 text over 64 symbols, 20% zero runs "
+            "4-64 KiB, 1 MiB blocks); RAM, AE, MAXP x mean {4,8,16} KiB, min=mean/4, max=8*mean")
+
+
+def wtable():
+    with open(os.path.join(ROOT, "tests", "golden", "wtable.json")) as f:
+        return json.load(f)
+
+
+def configs():
+    t = wtable()["mixed_4g_seed1"]
+    return [(alg, mean, t[alg][str(mean)]["w"], t[alg][str(mean)]["min"], t[alg][str(mean)]["max"])
+            for alg in ALGS for mean in MEANS]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic():
+    """dram bytes per input byte of the summary kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "summary_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None, None
+    with open(p) as f:
+        d = json.load(f)
+    src = os.path.join(ROOT, "paper_2508_05797_gb300", "csrc", "summarize.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if d.get("source_sha256_16") != h:
+        return None, d
+    return d, d
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            torch.cuda.set_device(local)
+        except Exception:
+            pass
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(sample_bytes: int = 256 * MIB):
+    """The oracle, single-threaded on a host core, over the first sample_bytes
+    of the stream for all nine (algorithm, mean) pairs."""
+    import oracle
+    import synth
+    data = synth.mixed_range(1, STREAM_LEN, 0, sample_bytes)
+    t0 = time.perf_counter()
+    for alg, mean, w, mn, mx in configs():
+        oracle.count(alg, data, w, mn, mx)
+    dt = time.perf_counter() - t0
+    return {"value": round(9 * sample_bytes / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d MiB of the 4 GiB mixed stream, all 9 (alg, mean) pairs, one thread" % (
+                sample_bytes // MIB), "seconds": round(dt, 2)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    sample = 32 * MIB
+    data = synth.mixed_range(1, STREAM_LEN, 0, sample)
+    cfg = configs()
+
+    def step():
+        for alg, mean, w, mn, mx in cfg:
+            oracle.count(alg, data, w, mn, mx)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    gbs = 9 * sample * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "sample_bytes_per_step": 9 * sample},
+            "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "first 32 MiB of the 4 GiB mixed stream per (alg, mean) pair, one thread"},
+            "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2508_05797_gb300 import Chunker
+    from paper_2508_05797_gb300.cdc import OPT_PROFILE
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seed = 1 + rank
+    host = torch.empty(STREAM_LEN, dtype=torch.uint8, pin_memory=True)
+    synth.mixed_range(seed, STREAM_LEN, 0, STREAM_LEN, out=host.numpy())
+    data = host.to(dev, non_blocking=False)
+    cfg = configs()
+    handles, outs, counts = [], [], []
+    for alg, mean, w, mn, mx in cfg:
+        ck = Chunker(local)
+        ck.reserve(alg, w, mn, mx, STREAM_LEN)
+        handles.append(ck)
+        outs.append(torch.empty(STREAM_LEN // mn + 1, dtype=torch.int64, device=dev))
+        counts.append(torch.zeros(1, dtype=torch.int64, device=dev))
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for (alg, mean, w, mn, mx), ck, o, c in zip(cfg, handles, outs, counts):
+            ck.chunk_async(data, alg, w, mn, mx, o, c, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    for ck in handles:
+        ck.sync_status(stream)
+        ck.set_option(OPT_PROFILE, 1)
+    sampler = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms = allreduce_max(ms, world)
+    for ck in handles:
+        ck.sync_status(stream)
+    per_cfg = []
+    launches = 0
+    sum_ms_total = 0.0
+    for (alg, mean, w, mn, mx), ck, c in zip(cfg, handles, counts):
+        calls, sms, cms, l = ck.profile_collect()
+        ck.set_option(OPT_PROFILE, 0)
+        launches += l
+        sum_ms_total += sms
+        per_cfg.append({"alg": alg, "mean": mean, "w": w, "calls": calls, "summary_ms": sms / max(calls, 1),
+                        "chain_ms": cms / max(calls, 1), "boundaries": int(c.item())})
+    total_bytes = 9 * STREAM_LEN * args.steps * world
+    gbs = total_bytes / (ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    per_alg = {}
+    for alg in ALGS:
+        rows = [r for r in per_cfg if r["alg"] == alg]
+        t = sum(r["summary_ms"] + r["chain_ms"] for r in rows)
+        per_alg[alg] = {"GBps": round(len(rows) * STREAM_LEN / (t / 1e3) / 1e9, 1),
+                        "hbm_frac": round(len(rows) * STREAM_LEN / (t / 1e3) / 1e9 / peak, 4),
+                        "summary_ms": [round(r["summary_ms"], 4) for r in rows],
+                        "chain_ms": [round(r["chain_ms"], 4) for r in rows]}
+    # roofline of the dominant kernel (block summaries: reads every input byte once)
+    summ_avg_ms = sum_ms_total / max(1, 9 * args.steps)
+    achieved = STREAM_LEN / (summ_avg_ms / 1e3) / 1e9
+    prof, _ = profile_traffic()
+    traffic = None
+    if prof:
+        traffic = int(prof["dram_bytes_per_input_byte"] * STREAM_LEN)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "k_summary_max / k_summary_maxp (stage 1, block summaries)",
+                "algorithmic_bytes_per_launch": STREAM_LEN}
+    line = {"metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "bytes_per_step": 9 * STREAM_LEN,
+                       "l2": "inputs larger than L2 (4 GiB per call, 129 MB L2)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "hbm_frac": round(gbs / world / peak, 4), "per_alg": per_alg, "roofline": roofline,
+            "gpu_launches": int(launches), "clocks": clocks}
+    # end to end through the host entry point (pinned host memory in, host boundaries out)
+    if not args.no_e2e:
+        outs_h = [np.empty(STREAM_LEN // mn + 1, dtype=np.uint64) for (_, _, _, mn, _) in cfg]
+        hnp = host.numpy()
+        d2h = 0
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            d2h = 0
+            for (alg, mean, w, mn, mx), ck, oh in zip(cfg, handles, outs_h):
+                b = ck.chunk_host(hnp, alg, w, mn, mx, out=oh, stream=stream)
+                d2h += b.size * 8
+        torch.cuda.synchronize()
+        dt = allreduce_max(time.perf_counter() - t0, world)
+        line["e2e"] = {"value": round(9 * STREAM_LEN * e2e_steps * world / dt / 1e9, 2), "unit": "GB/s",
+                       "h2d_bytes_per_step": 9 * STREAM_LEN, "d2h_bytes_per_step": int(d2h),
+                       "steps": e2e_steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for ck in handles:
+        ck.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

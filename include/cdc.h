@@ -1,0 +1,183 @@
+/*
+ * cdc.h -- C ABI of the GB300 hashless content-defined chunking library.
+ *
+ * The library finds chunk boundaries with the hashless algorithms RAM,
+ * AE (AE-Max and AE-Min) and MAXP of arxiv 2508.05797 ("VectorCDC"):
+ *   RAM  -- Section 2.1 (RAM paragraph), Section 3.3: the maximum of the
+ *           w-byte window at the chunk start, then the first later byte that
+ *           is >= that maximum ends the chunk (the byte is inside the chunk).
+ *   AE   -- Section 2.1 (AE paragraph), Section 3.3: a target is a byte
+ *           beyond (greater for AE-Max, lower for AE-Min) all bytes before it
+ *           in the chunk; once the w bytes after a target hold nothing beyond
+ *           it, the chunk ends right after those w bytes.
+ *   MAXP -- Section 2.1 (MAXP paragraph), Section 3.3: a target is strictly
+ *           greater than every byte within distance w on both sides (both
+ *           windows inside the data); the chunk ends right after the first
+ *           target that gives at least `min` bytes.
+ * min / max bound the chunk size as in Section 2.1 (hash-based paragraph):
+ * no cut before min bytes, a forced cut at max bytes; the last chunk ends at
+ * the end of the data and may be shorter than min.
+ *
+ * Output: the increasing list of chunk ends b_1 < ... < b_k = len (offsets
+ * from the start of the data), so chunk i is [b_{i-1}, b_i) with b_0 = 0.
+ * The boundaries equal, bit for bit, those of the plain sequential algorithm
+ * (the paper's own criterion, Section 5.2: accelerated and native chunks
+ * are identical).
+ *
+ * Conventions for every entry point:
+ *   - Data and output buffers are caller-owned DEVICE memory unless the name
+ *     says host. Any alignment is accepted.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
+ *     enqueued on it; entry points that return a count synchronise it.
+ *   - A handle owns device workspace and is not thread-safe: use one handle
+ *     per host thread (or serialise calls). Workspace grows on demand
+ *     outside the hot path; while a stream is being captured into a CUDA
+ *     graph the workspace must already be large enough (else
+ *     CDC_ERR_NOMEM).
+ *   - Errors are returned, never printed; cdc_status_string() names them.
+ *   - Parameter rules (CDC_ERR_INVALID otherwise): w >= 1, 1 <= min <= max,
+ *     and for RAM / AE w < max. A NULL data pointer with len > 0, a NULL
+ *     output pointer, an unknown algorithm or an unknown option is invalid.
+ */
+#ifndef CDC_H
+#define CDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CDC_API __attribute__((visibility("default")))
+#else
+#define CDC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CDC_RAM = 0,     /* Rapid Asymmetric Maximum */
+    CDC_AE = 1,      /* Asymmetric Extremum, maxima (AE-Max) */
+    CDC_MAXP = 2,    /* local maximum over +-w */
+    CDC_AE_MIN = 3   /* Asymmetric Extremum, minima (AE-Min) */
+} cdc_alg;
+
+typedef struct {
+    uint32_t w;      /* window size in bytes */
+    uint32_t min;    /* minimum chunk size in bytes */
+    uint32_t max;    /* maximum chunk size in bytes */
+} cdc_params;
+
+typedef enum {
+    CDC_OK = 0,
+    CDC_ERR_INVALID = 1,   /* bad argument */
+    CDC_ERR_CAPACITY = 2,  /* output too small; the count holds the size needed */
+    CDC_ERR_CUDA = 3,      /* a CUDA call failed (no device, launch error, ...) */
+    CDC_ERR_TIMEOUT = 4,   /* a bounded device-side wait ran out */
+    CDC_ERR_NOMEM = 5,     /* workspace could not be allocated */
+    CDC_ERR_INTERNAL = 6   /* a device-side consistency check failed */
+} cdc_status;
+
+typedef struct cdc_handle_s* cdc_handle;
+typedef void* cdc_stream;  /* a cudaStream_t */
+
+/* Create a handle on CUDA device `device` (which becomes current for the
+ * calling thread). *out receives the handle; nothing is allocated on the
+ * device until first use. */
+CDC_API cdc_status cdc_create(cdc_handle* out, int device);
+
+/* Release the handle and its device workspace. NULL is accepted. */
+CDC_API cdc_status cdc_destroy(cdc_handle h);
+
+/* Chunk one device buffer `data` of `len` bytes with algorithm `alg`.
+ * out_bounds: device array receiving the chunk ends (uint64, offsets from
+ * data). *n: on entry its capacity in elements, on return the number of
+ * boundaries (also when CDC_ERR_CAPACITY is returned, in which case the
+ * contents of out_bounds are unspecified). len == 0 gives *n = 0.
+ * Synchronises `stream`. */
+CDC_API cdc_status cdc_chunk(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
+                     uint64_t* out_bounds, size_t* n, cdc_stream stream);
+
+/* As cdc_chunk, without synchronising: the boundary count (uint64) is
+ * written to the device word *d_count when the work completes. A count
+ * above `capacity` means the output was too small (contents unspecified);
+ * device-side errors are reported by the next cdc_chunk / cdc_sync_status
+ * call on the handle. Capturable into a CUDA graph once the workspace is
+ * sized (call cdc_reserve first). */
+CDC_API cdc_status cdc_chunk_async(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data,
+                           size_t len, uint64_t* out_bounds, size_t capacity,
+                           uint64_t* d_count, cdc_stream stream);
+
+/* Chunk many files packed in one device arena in a single persistent
+ * launch. File f is data[file_off[f], file_off[f+1]) and is chunked from its
+ * own start. data_len: bytes of the arena (>= file_off[n_files]).
+ * d_file_off: device array of n_files + 1 non-decreasing offsets.
+ * d_bounds: device array receiving every file's boundaries, file after file,
+ * each relative to its file's start. d_bounds_index: device array of
+ * n_files + 1 entries; file f's boundaries are
+ * d_bounds[d_bounds_index[f] .. d_bounds_index[f+1]). capacity: elements of
+ * d_bounds. total: if not NULL, receives the total count and the stream is
+ * synchronised; if NULL the call is asynchronous (the total is then
+ * d_bounds_index[n_files]). */
+CDC_API cdc_status cdc_chunk_batch(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data,
+                           size_t data_len, const uint64_t* d_file_off, size_t n_files,
+                           uint64_t* d_bounds, uint64_t* d_bounds_index, size_t capacity,
+                           size_t* total, cdc_stream stream);
+
+/* End-to-end call on HOST buffers: copies `host_data` to the device, chunks
+ * it and copies the boundaries back into host_bounds (capacity *n; *n
+ * receives the count). Page-locked host memory gives the fastest copies.
+ * Synchronises `stream`. */
+CDC_API cdc_status cdc_chunk_host(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* host_data,
+                          size_t len, uint64_t* host_bounds, size_t* n, cdc_stream stream);
+
+/* Make sure the workspace fits `len` bytes of data in up to `n_files` files
+ * for algorithm `alg` and parameters p (so that later calls allocate
+ * nothing, e.g. before graph capture). */
+CDC_API cdc_status cdc_reserve(cdc_handle h, cdc_alg alg, cdc_params p, size_t len, size_t n_files);
+
+/* Wait for the work on `stream` and report device-side errors of the
+ * asynchronous calls made on the handle since the last check. */
+CDC_API cdc_status cdc_sync_status(cdc_handle h, cdc_stream stream);
+
+/* Tuning and test options (value semantics per option). */
+typedef enum {
+    CDC_OPT_SEGMENT = 0,      /* bytes per speculative segment; 0 = automatic */
+    CDC_OPT_SPAN = 1,         /* bytes over which a segment's 32 speculative
+                                 chains start; 0 = automatic */
+    CDC_OPT_TIMEOUT_MS = 2,   /* bound on any device-side wait (default 2000) */
+    CDC_OPT_FORCE_BYTES = 3,  /* 1 = skip the block summaries and scan raw
+                                 bytes in the chain stage (testing) */
+    CDC_OPT_DEBUG_HOLD_ITEM = 4, /* testing only: the segment with this index
+                                 never publishes its state, so its successors
+                                 time out (-1 = off, the default) */
+    CDC_OPT_PROFILE = 5       /* 1 = record CUDA events around the stages of
+                                 every call (up to 1024 calls) for
+                                 cdc_profile_collect; setting it clears them */
+} cdc_option;
+
+CDC_API cdc_status cdc_set_option(cdc_handle h, cdc_option opt, int64_t value);
+CDC_API cdc_status cdc_get_option(cdc_handle h, cdc_option opt, int64_t* value);
+
+/* Device time in milliseconds of the two stages of the last call on the
+ * handle (block summaries; chain), measured with CUDA events on the call's
+ * stream. Synchronises on those events. Either pointer may be NULL. */
+CDC_API cdc_status cdc_last_timing(cdc_handle h, float* summary_ms, float* chain_ms);
+
+/* Totals over the calls recorded since profiling was switched on or last
+ * collected: number of calls, device milliseconds of the summary stage and of
+ * the chain stage, and kernels launched. Synchronises on the recorded events
+ * and clears them. Any output pointer may be NULL. */
+CDC_API cdc_status cdc_profile_collect(cdc_handle h, int* calls, double* summary_ms, double* chain_ms,
+                                       int64_t* launches);
+
+/* Number of kernels the last call launched. */
+CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
+
+CDC_API const char* cdc_status_string(cdc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDC_H */

@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) hashless content-defined chunking: RAM, AE, MAXP.
+
+The work runs in libcdc.so (CUDA; C ABI in include/cdc.h); this package is
+its Python binding. See ``cdc.Chunker`` and ``cdc.chunk``.
+"""
+from .cdc import (ALGS, CdcError, Chunker, Params, chunk, chunk_batch, default_chunker, exported_symbols,
+                  library_path, load_library, max_boundaries)
+
+__all__ = ["ALGS", "CdcError", "Chunker", "Params", "chunk", "chunk_batch", "default_chunker",
+           "exported_symbols", "library_path", "load_library", "max_boundaries"]

@@ -1,0 +1,232 @@
+"""ctypes binding of libcdc.so (include/cdc.h) with torch tensors for device memory.
+
+Argument marshalling only: every step of chunking runs in the CUDA library.
+If the library cannot be built or loaded, every call raises; there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+ALGS = {"ram": 0, "ae": 1, "ae_max": 1, "maxp": 2, "ae_min": 3}
+OPT_SEGMENT, OPT_SPAN, OPT_TIMEOUT_MS, OPT_FORCE_BYTES, OPT_DEBUG_HOLD_ITEM = range(5)
+OPT_PROFILE = 5
+STATUS = ["CDC_OK", "CDC_ERR_INVALID", "CDC_ERR_CAPACITY", "CDC_ERR_CUDA", "CDC_ERR_TIMEOUT",
+          "CDC_ERR_NOMEM", "CDC_ERR_INTERNAL"]
+OK, ERR_INVALID, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_INTERNAL = range(7)
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CdcError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        name = STATUS[status] if 0 <= status < len(STATUS) else "status %d" % status
+        super().__init__("%s%s" % (name, (": " + what) if what else ""))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_uint32), ("min", ctypes.c_uint32), ("max", ctypes.c_uint32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libcdc.so (building it first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libcdc.so is missing at %s; build it with "
+                               "paper_2508_05797_gb300.build.build()" % path)
+        lib = ctypes.CDLL(path)
+        vp, sz, u64, i32, i64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int, ctypes.c_int64
+        P = Params
+        sig = {
+            "cdc_create": ([ctypes.POINTER(vp), i32], i32),
+            "cdc_destroy": ([vp], i32),
+            "cdc_chunk": ([vp, i32, P, vp, sz, vp, ctypes.POINTER(sz), vp], i32),
+            "cdc_chunk_async": ([vp, i32, P, vp, sz, vp, sz, vp, vp], i32),
+            "cdc_chunk_batch": ([vp, i32, P, vp, sz, vp, sz, vp, vp, sz, ctypes.POINTER(sz), vp], i32),
+            "cdc_chunk_host": ([vp, i32, P, vp, sz, vp, ctypes.POINTER(sz), vp], i32),
+            "cdc_reserve": ([vp, i32, P, sz, sz], i32),
+            "cdc_sync_status": ([vp, vp], i32),
+            "cdc_set_option": ([vp, i32, i64], i32),
+            "cdc_get_option": ([vp, i32, ctypes.POINTER(i64)], i32),
+            "cdc_last_timing": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)], i32),
+            "cdc_last_launches": ([vp, ctypes.POINTER(i32)], i32),
+            "cdc_profile_collect": ([vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
+            "cdc_status_string": ([i32], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def exported_symbols() -> list[str]:
+    return ["cdc_create", "cdc_destroy", "cdc_chunk", "cdc_chunk_async", "cdc_chunk_batch", "cdc_chunk_host",
+            "cdc_reserve", "cdc_sync_status", "cdc_set_option", "cdc_get_option", "cdc_last_timing",
+            "cdc_last_launches", "cdc_profile_collect", "cdc_status_string"]
+
+
+def alg_id(alg) -> int:
+    return ALGS[alg.lower()] if isinstance(alg, str) else int(alg)
+
+
+def _check(st: int, what: str = ""):
+    if st != OK:
+        raise CdcError(st, what)
+
+
+def _stream_handle(stream) -> int | None:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def max_boundaries(n: int, mn: int) -> int:
+    """Upper bound on the number of chunks of n bytes: all but the last are >= min."""
+    return n // max(mn, 1) + 1
+
+
+class Chunker:
+    """One library handle on one CUDA device (not thread-safe)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(self.lib.cdc_create(ctypes.byref(h), device), "cdc_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.cdc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # options
+    def set_option(self, opt: int, value: int):
+        _check(self.lib.cdc_set_option(self.h, opt, int(value)), "cdc_set_option")
+
+    def get_option(self, opt: int) -> int:
+        v = ctypes.c_int64()
+        _check(self.lib.cdc_get_option(self.h, opt, ctypes.byref(v)), "cdc_get_option")
+        return v.value
+
+    def last_timing(self):
+        a, b = ctypes.c_float(), ctypes.c_float()
+        _check(self.lib.cdc_last_timing(self.h, ctypes.byref(a), ctypes.byref(b)), "cdc_last_timing")
+        return a.value, b.value
+
+    def last_launches(self) -> int:
+        n = ctypes.c_int()
+        _check(self.lib.cdc_last_launches(self.h, ctypes.byref(n)))
+        return n.value
+
+    def profile_collect(self):
+        """(calls, summary ms, chain ms, kernel launches) recorded since the last collect."""
+        n, a, b, l = ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        _check(self.lib.cdc_profile_collect(self.h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(b),
+                                            ctypes.byref(l)), "cdc_profile_collect")
+        return n.value, a.value, b.value, l.value
+
+    # chunking
+    def chunk(self, data, alg, w: int, mn: int, mx: int, out=None, stream=None):
+        """Boundaries of a uint8 CUDA tensor as an int64 CUDA tensor."""
+        import torch
+        assert data.dtype == torch.uint8 and data.is_cuda and data.is_contiguous()
+        n = data.numel()
+        if out is None:
+            out = torch.empty(max_boundaries(n, mn), dtype=torch.int64, device=data.device)
+        cap = ctypes.c_size_t(out.numel())
+        st = self.lib.cdc_chunk(self.h, alg_id(alg), Params(w, mn, mx), data.data_ptr() if n else None, n,
+                                out.data_ptr(), ctypes.byref(cap), _stream_handle(stream))
+        _check(st, "cdc_chunk (count %d)" % cap.value)
+        return out[:cap.value]
+
+    def chunk_async(self, data, alg, w: int, mn: int, mx: int, out, d_count, stream=None):
+        import torch
+        assert data.dtype == torch.uint8 and data.is_cuda and data.is_contiguous()
+        st = self.lib.cdc_chunk_async(self.h, alg_id(alg), Params(w, mn, mx), data.data_ptr(), data.numel(),
+                                      out.data_ptr(), out.numel(), d_count.data_ptr(), _stream_handle(stream))
+        _check(st, "cdc_chunk_async")
+
+    def chunk_batch(self, arena, file_off, alg, w: int, mn: int, mx: int, out=None, index=None,
+                    stream=None, sync: bool = True):
+        """Chunk every file of a packed arena. file_off: int64 CUDA tensor of
+        n_files + 1 offsets. Returns (boundaries, index) with file f's
+        boundaries at boundaries[index[f]:index[f+1]] (relative to its start)."""
+        import torch
+        assert arena.dtype == torch.uint8 and arena.is_cuda
+        n_files = file_off.numel() - 1
+        if out is None:
+            out = torch.empty(arena.numel() // max(mn, 1) + n_files + 1, dtype=torch.int64, device=arena.device)
+        if index is None:
+            index = torch.empty(n_files + 1, dtype=torch.int64, device=arena.device)
+        total = ctypes.c_size_t(0)
+        st = self.lib.cdc_chunk_batch(self.h, alg_id(alg), Params(w, mn, mx), arena.data_ptr(), arena.numel(),
+                                      file_off.data_ptr(), n_files, out.data_ptr(), index.data_ptr(), out.numel(),
+                                      ctypes.byref(total) if sync else None, _stream_handle(stream))
+        _check(st, "cdc_chunk_batch (total %d)" % total.value)
+        return (out[:total.value] if sync else out), index
+
+    def chunk_host(self, data, alg, w: int, mn: int, mx: int, out=None, stream=None):
+        """End to end from a host numpy uint8 array to a host numpy uint64 array."""
+        import numpy as np
+        assert data.dtype == np.uint8 and data.flags.c_contiguous
+        n = data.size
+        if out is None:
+            out = np.empty(max_boundaries(n, mn), dtype=np.uint64)
+        cap = ctypes.c_size_t(out.size)
+        st = self.lib.cdc_chunk_host(self.h, alg_id(alg), Params(w, mn, mx), data.ctypes.data, n,
+                                     out.ctypes.data, ctypes.byref(cap), _stream_handle(stream))
+        _check(st, "cdc_chunk_host (count %d)" % cap.value)
+        return out[:cap.value]
+
+    def reserve(self, alg, w: int, mn: int, mx: int, n: int, n_files: int = 0):
+        _check(self.lib.cdc_reserve(self.h, alg_id(alg), Params(w, mn, mx), n, n_files), "cdc_reserve")
+
+    def sync_status(self, stream=None):
+        _check(self.lib.cdc_sync_status(self.h, _stream_handle(stream)), "device-side status")
+
+
+_default: dict = {}
+
+
+def default_chunker(device: int | None = None) -> Chunker:
+    import torch
+    d = torch.cuda.current_device() if device is None else device
+    if d not in _default:
+        _default[d] = Chunker(d)
+    return _default[d]
+
+
+def chunk(data, alg, w: int, mn: int, mx: int, stream=None):
+    """Boundaries (int64 CUDA tensor) of a uint8 CUDA tensor on the current stream."""
+    return default_chunker(data.device.index).chunk(data, alg, w, mn, mx, stream=stream)
+
+
+def chunk_batch(arena, file_off, alg, w: int, mn: int, mx: int, stream=None):
+    return default_chunker(arena.device.index).chunk_batch(arena, file_off, alg, w, mn, mx, stream=stream)

@@ -1,0 +1,538 @@
+// api.cu -- the C ABI (include/cdc.h): handles, workspace, validation and the
+// launch sequence  [batch set-up] -> summaries (or control reset) -> chain.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "../../include/cdc.h"
+#include "cdc_device.cuh"
+#include "cdc_launch.h"
+
+using namespace cdc;
+
+struct cdc_handle_s {
+    int device = 0;
+    int sm_count = 0;
+    // workspace (grow-only)
+    uint8_t* smax = nullptr;
+    uint8_t* sarg = nullptr;
+    size_t sum_cap = 0;  // bytes of smax
+    size_t sarg_cap = 0;
+    ItemStatus* st = nullptr;
+    size_t st_cap = 0;   // items
+    Ctrl* ctrl = nullptr;
+    uint64_t* item_off = nullptr;
+    uint64_t* scan_tmp = nullptr;
+    size_t scan_cap = 0;
+    size_t files_cap = 0;
+    uint32_t* item_file = nullptr;
+    size_t item_file_cap = 0;
+    uint8_t* host_stage = nullptr;  // cdc_chunk_host device copies
+    size_t host_stage_cap = 0;
+    uint64_t* host_out = nullptr;
+    size_t host_out_cap = 0;
+    Ctrl* pinned_ctrl = nullptr;  // page-locked copy of the control block
+    // options
+    int64_t seg = 0, span = 0, timeout_ms = 2000, force_bytes = 0, hold_item = -1;
+    // last-call bookkeeping
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool timed = false;
+    int launches = 0;
+    // profiling ring: event triples of up to PROF_CAP calls
+    static constexpr int PROF_CAP = 1024;
+    int64_t profile = 0;
+    cudaEvent_t* prof_ev = nullptr;
+    int prof_n = 0;
+    int64_t prof_launches = 0;
+    cudaEvent_t* last_ev = nullptr;
+};
+
+static const char* kStatusNames[] = {"CDC_OK", "CDC_ERR_INVALID", "CDC_ERR_CAPACITY", "CDC_ERR_CUDA",
+                                     "CDC_ERR_TIMEOUT", "CDC_ERR_NOMEM", "CDC_ERR_INTERNAL"};
+
+extern "C" const char* cdc_status_string(cdc_status s) {
+    if ((int)s >= 0 && (int)s < 7) return kStatusNames[(int)s];
+    return "CDC_ERR_UNKNOWN";
+}
+
+static bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return false;
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+template <typename T>
+static cdc_status grow(T** p, size_t* cap, size_t need, bool zero, cudaStream_t s) {
+    if (*cap >= need && *p) return CDC_OK;
+    if (capturing(s)) return CDC_ERR_NOMEM;
+    size_t n = need + need / 4 + 64;
+    if (*p) {
+        cudaStreamSynchronize(s);
+        cudaFree(*p);
+        *p = nullptr;
+        *cap = 0;
+    }
+    T* q = nullptr;
+    if (cudaMalloc(&q, n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return CDC_ERR_NOMEM;
+    }
+    if (zero && cudaMemset(q, 0, n * sizeof(T)) != cudaSuccess) {
+        cudaFree(q);
+        return CDC_ERR_CUDA;
+    }
+    *p = q;
+    *cap = n;
+    return CDC_OK;
+}
+
+extern "C" cdc_status cdc_create(cdc_handle* out, int device) {
+    if (!out) return CDC_ERR_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return CDC_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return CDC_ERR_CUDA;
+    cdc_handle h = new cdc_handle_s();
+    h->device = device;
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&h->ctrl, sizeof(Ctrl)) != cudaSuccess || cudaMemset(h->ctrl, 0, sizeof(Ctrl)) != cudaSuccess ||
+        cudaMallocHost(&h->pinned_ctrl, sizeof(Ctrl)) != cudaSuccess) {
+        cudaGetLastError();
+        cdc_destroy(h);
+        return CDC_ERR_NOMEM;
+    }
+    for (int i = 0; i < 3; i++) cudaEventCreate(&h->ev[i]);
+    *out = h;
+    return CDC_OK;
+}
+
+extern "C" cdc_status cdc_destroy(cdc_handle h) {
+    if (!h) return CDC_OK;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    cudaFree(h->smax);
+    cudaFree(h->sarg);
+    cudaFree(h->st);
+    cudaFree(h->ctrl);
+    cudaFree(h->item_off);
+    cudaFree(h->scan_tmp);
+    cudaFree(h->item_file);
+    cudaFree(h->host_stage);
+    cudaFree(h->host_out);
+    if (h->pinned_ctrl) cudaFreeHost(h->pinned_ctrl);
+    for (int i = 0; i < 3; i++)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    if (h->prof_ev) {
+        for (int i = 0; i < 3 * cdc_handle_s::PROF_CAP; i++) cudaEventDestroy(h->prof_ev[i]);
+        free(h->prof_ev);
+    }
+    cudaGetLastError();
+    delete h;
+    return CDC_OK;
+}
+
+extern "C" cdc_status cdc_set_option(cdc_handle h, cdc_option opt, int64_t v) {
+    if (!h) return CDC_ERR_INVALID;
+    switch (opt) {
+    case CDC_OPT_SEGMENT:
+        if (v < 0 || v > (1ll << 24) || (v && v < 64)) return CDC_ERR_INVALID;
+        h->seg = v;
+        return CDC_OK;
+    case CDC_OPT_SPAN:
+        if (v < 0) return CDC_ERR_INVALID;
+        h->span = v;
+        return CDC_OK;
+    case CDC_OPT_TIMEOUT_MS:
+        if (v <= 0) return CDC_ERR_INVALID;
+        h->timeout_ms = v;
+        return CDC_OK;
+    case CDC_OPT_FORCE_BYTES: h->force_bytes = v ? 1 : 0; return CDC_OK;
+    case CDC_OPT_DEBUG_HOLD_ITEM: h->hold_item = v; return CDC_OK;
+    case CDC_OPT_PROFILE:
+        if (v && !h->prof_ev) {
+            cudaSetDevice(h->device);
+            h->prof_ev = (cudaEvent_t*)calloc(3 * cdc_handle_s::PROF_CAP, sizeof(cudaEvent_t));
+            if (!h->prof_ev) return CDC_ERR_NOMEM;
+            for (int i = 0; i < 3 * cdc_handle_s::PROF_CAP; i++)
+                if (cudaEventCreate(&h->prof_ev[i]) != cudaSuccess) return CDC_ERR_CUDA;
+        }
+        h->profile = v ? 1 : 0;
+        h->prof_n = 0;
+        h->prof_launches = 0;
+        return CDC_OK;
+    default: return CDC_ERR_INVALID;
+    }
+}
+
+extern "C" cdc_status cdc_get_option(cdc_handle h, cdc_option opt, int64_t* v) {
+    if (!h || !v) return CDC_ERR_INVALID;
+    switch (opt) {
+    case CDC_OPT_SEGMENT: *v = h->seg; return CDC_OK;
+    case CDC_OPT_SPAN: *v = h->span; return CDC_OK;
+    case CDC_OPT_TIMEOUT_MS: *v = h->timeout_ms; return CDC_OK;
+    case CDC_OPT_FORCE_BYTES: *v = h->force_bytes; return CDC_OK;
+    case CDC_OPT_DEBUG_HOLD_ITEM: *v = h->hold_item; return CDC_OK;
+    case CDC_OPT_PROFILE: *v = h->profile; return CDC_OK;
+    default: return CDC_ERR_INVALID;
+    }
+}
+
+static bool valid_params(cdc_alg alg, cdc_params p) {
+    if ((int)alg < 0 || (int)alg > 3) return false;
+    if (p.w < 1 || p.min < 1 || p.min > p.max) return false;
+    if (alg != CDC_MAXP && p.w >= p.max) return false;
+    return true;
+}
+
+// which summaries and which chain rule a call uses
+struct Plan {
+    int sum;   // SumKind
+    int rule;  // Rule
+    uint32_t inv;
+    uint32_t halo;
+};
+
+static constexpr uint32_t MAXP_SUMMARY_MAX_W = 16384;
+
+static Plan make_plan(cdc_handle h, cdc_alg alg, cdc_params p) {
+    Plan pl{SUM_NONE, RULE_RAM_BYTES, 0u, 0u};
+    bool bytes = h->force_bytes != 0;
+    switch (alg) {
+    case CDC_RAM:
+        if (!bytes) { pl.sum = SUM_MAX; pl.rule = RULE_RAM; }
+        else pl.rule = RULE_RAM_BYTES;
+        break;
+    case CDC_AE:
+    case CDC_AE_MIN:
+        pl.inv = alg == CDC_AE_MIN ? 0xFFFFFFFFu : 0u;
+        if (!bytes && p.w >= 64) {
+            pl.sum = alg == CDC_AE_MIN ? SUM_MAX_INV : SUM_MAX;
+            pl.rule = RULE_AE;
+        } else pl.rule = RULE_AE_BYTES;
+        break;
+    case CDC_MAXP:
+        if (!bytes && p.w >= 63 && p.w <= MAXP_SUMMARY_MAX_W) {
+            pl.sum = SUM_MAXP;
+            pl.rule = RULE_MAXP;
+            pl.halo = maxp_halo_blocks(p.w);
+        } else pl.rule = RULE_MAXP_BYTES;
+        break;
+    }
+    return pl;
+}
+
+// segment size: a few segments per resident warp, 64-byte multiple
+static uint64_t pick_seg(cdc_handle h, uint64_t len, uint64_t n_files) {
+    if (h->seg) return (uint64_t)h->seg;
+    uint64_t per = len / ((uint64_t)(h->sm_count > 0 ? h->sm_count : 148) * 16 + n_files);
+    uint64_t s = per < (32u << 10) ? (32u << 10) : per;
+    if (s > (256u << 10)) s = 256u << 10;
+    return (s + 63) & ~63ull;
+}
+
+static uint64_t pick_span(cdc_handle h, cdc_params p, uint64_t seg) {
+    uint64_t sp = h->span ? (uint64_t)h->span : (uint64_t)p.max / 8;
+    if (sp < 32) sp = 32;
+    if (sp > seg / 2) sp = seg / 2 > 32 ? seg / 2 : 32;
+    return sp;
+}
+
+static uint32_t pick_win(cdc_params p, uint64_t seg) {
+    uint64_t blocks = (seg + (uint64_t)p.max + 2 * 64) / 64 + 32;
+    blocks = (blocks + 15) & ~15ull;
+    const uint64_t cap = 24u << 10;  // bytes of shared memory per summary array
+    if (blocks > cap) blocks = cap;
+    return (uint32_t)blocks;
+}
+
+struct Geo {
+    const uint8_t* base;
+    uint64_t lo, hi, glo, ghi, nblk, nblk_pad;
+};
+
+static Geo geometry(const uint8_t* data, uint64_t len) {
+    Geo g;
+    uintptr_t a = (uintptr_t)data;
+    g.base = (const uint8_t*)(a & ~(uintptr_t)63);
+    g.lo = a & 63;
+    g.hi = g.lo + len;
+    g.glo = g.lo & ~15ull;
+    g.ghi = (g.hi + 15) & ~15ull;
+    g.nblk = (g.hi + 63) / 64;
+    g.nblk_pad = (g.nblk + 15) & ~15ull;
+    return g;
+}
+
+// launch the summary and chain stages; n_files == 0 means one stream
+static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data, uint64_t len,
+                      const uint64_t* d_file_off, uint64_t n_files, uint64_t* out, uint64_t capacity,
+                      uint64_t* bounds_index, uint64_t* d_count, cudaStream_t st) {
+    cudaSetDevice(h->device);
+    const Plan pl = make_plan(h, alg, p);
+    const Geo g = geometry(data, len);
+    const bool batch = d_file_off != nullptr;
+    const uint64_t seg = pick_seg(h, len, batch ? n_files : 1);
+    const uint64_t items = batch ? len / seg + n_files + 1 : (len + seg - 1) / seg;
+    cdc_status s;
+    if (pl.sum != SUM_NONE) {
+        const size_t need = g.nblk_pad + 64;
+        if ((s = grow(&h->smax, &h->sum_cap, need, false, st)) != CDC_OK) return s;
+        if (pl.sum != SUM_MAXP && (s = grow(&h->sarg, &h->sarg_cap, need, false, st)) != CDC_OK) return s;
+    }
+    if ((s = grow(&h->st, &h->st_cap, items, true, st)) != CDC_OK) return s;
+    if (batch) {
+        if ((s = grow(&h->item_off, &h->files_cap, n_files + 1, false, st)) != CDC_OK) return s;
+        if ((s = grow(&h->scan_tmp, &h->scan_cap, batch_scan_tmp_elems(n_files), false, st)) != CDC_OK) return s;
+        if ((s = grow(&h->item_file, &h->item_file_cap, items, false, st)) != CDC_OK) return s;
+    }
+    h->launches = 0;
+    const uint64_t timeout_ns = (uint64_t)h->timeout_ms * 1000000ull;
+    const bool rec = !capturing(st);
+    h->timed = false;
+    cudaEvent_t* ev = h->ev;
+    if (rec && h->profile && h->prof_n < cdc_handle_s::PROF_CAP) ev = h->prof_ev + 3 * h->prof_n++;
+    if (batch) {
+        if (launch_batch_setup(d_file_off, n_files, seg, h->item_off, h->item_file, h->scan_tmp, h->ctrl, st,
+                               &h->launches) != cudaSuccess)
+            return CDC_ERR_CUDA;
+    }
+    if (rec) cudaEventRecord(ev[0], st);
+    if (pl.sum != SUM_NONE) {
+        SumLaunch a;
+        a.base = g.base;
+        a.lo = g.lo; a.hi = g.hi; a.glo = g.glo; a.ghi = g.ghi;
+        a.nblk = g.nblk;
+        a.smax = h->smax;
+        a.sarg = h->sarg;
+        a.w = p.w;
+        a.halo_blocks = pl.halo;
+        a.timeout_ns = timeout_ns;
+        a.ctrl = h->ctrl;
+        uint64_t tiles = summary_tiles(pl.sum, g.nblk);
+        uint64_t grid = (uint64_t)h->sm_count * summary_blocks_per_sm(pl.sum, pl.halo);
+        if (grid > tiles) grid = tiles;
+        if (grid < 1) grid = 1;
+        if (launch_summary(a, pl.sum, (int)grid, st) != cudaSuccess) return CDC_ERR_CUDA;
+    } else {
+        if (launch_reset(h->ctrl, st) != cudaSuccess) return CDC_ERR_CUDA;
+    }
+    h->launches++;
+    if (rec) cudaEventRecord(ev[1], st);
+    ChainLaunch c;
+    memset(&c, 0, sizeof c);
+    c.base = g.base;
+    c.lo = g.lo;
+    c.hi = g.hi;
+    c.smax = h->smax;
+    c.sarg = h->sarg ? h->sarg : h->smax;
+    c.nblk_pad = g.nblk_pad;
+    c.w = p.w; c.mn = p.min; c.mx = p.max;
+    c.inv = pl.inv;
+    c.file_off = batch ? d_file_off : nullptr;
+    c.single_len = len;
+    c.n_files = batch ? n_files : 1;
+    c.item_off = batch ? h->item_off : nullptr;
+    c.item_file = batch ? h->item_file : nullptr;
+    c.n_items = items;
+    c.n_items_dev = batch ? &h->ctrl->n_items : nullptr;
+    c.seg = seg;
+    c.span = pick_span(h, p, seg);
+    c.win = pick_win(p, seg);
+    c.out = out;
+    c.capacity = capacity;
+    c.bounds_index = bounds_index;
+    c.d_count = d_count;
+    c.st = h->st;
+    c.ctrl = h->ctrl;
+    c.timeout_ns = timeout_ns;
+    c.hold_item = h->hold_item;
+    uint64_t grid = (uint64_t)h->sm_count * chain_blocks_per_sm(pl.rule, c.win);
+    if (grid > items) grid = items;
+    if (grid < 1) grid = 1;
+    if (launch_chain(c, pl.rule, (int)grid, st) != cudaSuccess) return CDC_ERR_CUDA;
+    h->launches++;
+    if (rec) {
+        cudaEventRecord(ev[2], st);
+        h->last_ev = ev;
+        h->timed = true;
+    }
+    h->prof_launches += h->launches;
+    return CDC_OK;
+}
+
+// read the control block, map device errors, clear them
+static cdc_status collect(cdc_handle h, cudaStream_t st, uint64_t* total) {
+    if (cudaMemcpyAsync(h->pinned_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return CDC_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CDC_ERR_CUDA;
+    if (total) *total = h->pinned_ctrl->total;
+    unsigned err = h->pinned_ctrl->err;
+    if (err) {
+        cudaMemsetAsync(&h->ctrl->err, 0, sizeof(unsigned), st);
+        cudaStreamSynchronize(st);
+        if (err & ERR_TIMEOUT) return CDC_ERR_TIMEOUT;
+        return CDC_ERR_INTERNAL;
+    }
+    return CDC_OK;
+}
+
+extern "C" cdc_status cdc_chunk(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
+                                uint64_t* out_bounds, size_t* n, cdc_stream stream) {
+    if (!h || !n || !valid_params(alg, p)) return CDC_ERR_INVALID;
+    if (len == 0) {
+        *n = 0;
+        return CDC_OK;
+    }
+    if (!data || !out_bounds) return CDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    cdc_status s = run(h, alg, p, data, len, nullptr, 0, out_bounds, *n, nullptr, nullptr, st);
+    if (s != CDC_OK) return s;
+    uint64_t total = 0;
+    s = collect(h, st, &total);
+    if (s != CDC_OK) return s;
+    size_t cap = *n;
+    *n = (size_t)total;
+    return total > cap ? CDC_ERR_CAPACITY : CDC_OK;
+}
+
+extern "C" cdc_status cdc_chunk_async(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
+                                      uint64_t* out_bounds, size_t capacity, uint64_t* d_count,
+                                      cdc_stream stream) {
+    if (!h || !d_count || !valid_params(alg, p)) return CDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (len == 0) {
+        return cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st) == cudaSuccess ? CDC_OK : CDC_ERR_CUDA;
+    }
+    if (!data || !out_bounds) return CDC_ERR_INVALID;
+    return run(h, alg, p, data, len, nullptr, 0, out_bounds, capacity, nullptr, d_count, st);
+}
+
+extern "C" cdc_status cdc_chunk_batch(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data,
+                                      size_t data_len, const uint64_t* d_file_off, size_t n_files,
+                                      uint64_t* d_bounds, uint64_t* d_bounds_index, size_t capacity,
+                                      size_t* total, cdc_stream stream) {
+    if (!h || !valid_params(alg, p) || !d_file_off || !d_bounds_index) return CDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n_files == 0 || data_len == 0) {
+        if (cudaMemsetAsync(d_bounds_index, 0, (n_files + 1) * sizeof(uint64_t), st) != cudaSuccess)
+            return CDC_ERR_CUDA;
+        if (total) {
+            *total = 0;
+            cudaStreamSynchronize(st);
+        }
+        return CDC_OK;
+    }
+    if (!data || !d_bounds || n_files > 0xFFFFFFFFull) return CDC_ERR_INVALID;
+    // d_bounds_index also covers the all-empty-files case: zero it first
+    if (cudaMemsetAsync(d_bounds_index, 0, (n_files + 1) * sizeof(uint64_t), st) != cudaSuccess) return CDC_ERR_CUDA;
+    cdc_status s = run(h, alg, p, data, data_len, d_file_off, n_files, d_bounds, capacity, d_bounds_index,
+                       nullptr, st);
+    if (s != CDC_OK || !total) return s;
+    uint64_t t = 0;
+    s = collect(h, st, &t);
+    if (s != CDC_OK) return s;
+    *total = (size_t)t;
+    return t > capacity ? CDC_ERR_CAPACITY : CDC_OK;
+}
+
+extern "C" cdc_status cdc_chunk_host(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* host_data, size_t len,
+                                     uint64_t* host_bounds, size_t* n, cdc_stream stream) {
+    if (!h || !n || !valid_params(alg, p)) return CDC_ERR_INVALID;
+    if (len == 0) {
+        *n = 0;
+        return CDC_OK;
+    }
+    if (!host_data || !host_bounds) return CDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaSetDevice(h->device);
+    cdc_status s;
+    if ((s = grow(&h->host_stage, &h->host_stage_cap, len, false, st)) != CDC_OK) return s;
+    size_t cap = *n;
+    if ((s = grow(&h->host_out, &h->host_out_cap, cap ? cap : 1, false, st)) != CDC_OK) return s;
+    if (cudaMemcpyAsync(h->host_stage, host_data, len, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return CDC_ERR_CUDA;
+    s = run(h, alg, p, h->host_stage, len, nullptr, 0, h->host_out, cap, nullptr, nullptr, st);
+    if (s != CDC_OK) return s;
+    uint64_t total = 0;
+    s = collect(h, st, &total);
+    if (s != CDC_OK) return s;
+    *n = (size_t)total;
+    if (total > cap) return CDC_ERR_CAPACITY;
+    if (cudaMemcpyAsync(host_bounds, h->host_out, total * sizeof(uint64_t), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return CDC_ERR_CUDA;
+    return CDC_OK;
+}
+
+extern "C" cdc_status cdc_reserve(cdc_handle h, cdc_alg alg, cdc_params p, size_t len, size_t n_files) {
+    if (!h || !valid_params(alg, p)) return CDC_ERR_INVALID;
+    cudaSetDevice(h->device);
+    const Plan pl = make_plan(h, alg, p);
+    const uint64_t nblk_pad = ((len + 64 + 63) / 64 + 15) & ~15ull;
+    const uint64_t seg = pick_seg(h, len, n_files ? n_files : 1);
+    const uint64_t items = len / seg + n_files + 2;
+    cdc_status s;
+    if (pl.sum != SUM_NONE) {
+        if ((s = grow(&h->smax, &h->sum_cap, nblk_pad + 64, false, 0)) != CDC_OK) return s;
+        if (pl.sum != SUM_MAXP && (s = grow(&h->sarg, &h->sarg_cap, nblk_pad + 64, false, 0)) != CDC_OK) return s;
+    }
+    if ((s = grow(&h->st, &h->st_cap, items, true, 0)) != CDC_OK) return s;
+    if (n_files) {
+        if ((s = grow(&h->item_off, &h->files_cap, n_files + 1, false, 0)) != CDC_OK) return s;
+        if ((s = grow(&h->scan_tmp, &h->scan_cap, batch_scan_tmp_elems(n_files), false, 0)) != CDC_OK) return s;
+        if ((s = grow(&h->item_file, &h->item_file_cap, items, false, 0)) != CDC_OK) return s;
+    }
+    return CDC_OK;
+}
+
+extern "C" cdc_status cdc_sync_status(cdc_handle h, cdc_stream stream) {
+    if (!h) return CDC_ERR_INVALID;
+    return collect(h, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" cdc_status cdc_last_timing(cdc_handle h, float* summary_ms, float* chain_ms) {
+    if (!h || !h->timed || !h->last_ev) return CDC_ERR_INVALID;
+    cudaEvent_t* ev = h->last_ev;
+    if (cudaEventSynchronize(ev[2]) != cudaSuccess) return CDC_ERR_CUDA;
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b, ev[1], ev[2]);
+    if (summary_ms) *summary_ms = a;
+    if (chain_ms) *chain_ms = b;
+    return CDC_OK;
+}
+
+extern "C" cdc_status cdc_last_launches(cdc_handle h, int* launches) {
+    if (!h || !launches) return CDC_ERR_INVALID;
+    *launches = h->launches;
+    return CDC_OK;
+}
+
+extern "C" cdc_status cdc_profile_collect(cdc_handle h, int* calls, double* summary_ms, double* chain_ms,
+                                          int64_t* launches) {
+    if (!h) return CDC_ERR_INVALID;
+    double a = 0, b = 0;
+    for (int i = 0; i < h->prof_n; i++) {
+        cudaEvent_t* ev = h->prof_ev + 3 * i;
+        if (cudaEventSynchronize(ev[2]) != cudaSuccess) return CDC_ERR_CUDA;
+        float x = 0, y = 0;
+        cudaEventElapsedTime(&x, ev[0], ev[1]);
+        cudaEventElapsedTime(&y, ev[1], ev[2]);
+        a += x;
+        b += y;
+    }
+    if (calls) *calls = h->prof_n;
+    if (summary_ms) *summary_ms = a;
+    if (chain_ms) *chain_ms = b;
+    if (launches) *launches = h->prof_launches;
+    h->prof_n = 0;
+    h->prof_launches = 0;
+    h->last_ev = nullptr;
+    h->timed = false;
+    return CDC_OK;
+}

@@ -1,0 +1,117 @@
+// cdc_device.cuh -- device-side structures and PTX helpers shared by the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "chain_logic.cuh"
+
+namespace cdc {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr int KFIRST = 8;  // chain positions per lane kept for stitching
+
+// Control block of a handle (device memory, one per handle).
+struct Ctrl {
+    unsigned long long ticket;   // next segment to take (dynamic, launch order)
+    unsigned long long total;    // number of boundaries (written by the last segment)
+    unsigned long long n_items;  // segments of a batch (written by the batch set-up)
+    unsigned long long err_info; // first failing item / position, for diagnostics
+    unsigned int epoch;          // launch number; a flag is set when it equals this
+    unsigned int err;            // sticky error bits, cleared by the host
+    unsigned int pad[6];
+};
+enum : unsigned int { ERR_TIMEOUT = 1u, ERR_INTERNAL = 2u };
+
+// Published state of one segment ("item"). Flags hold the epoch of the
+// launch that set them, so stale state from an earlier launch never matches.
+struct __align__(128) ItemStatus {
+    // phase A: 32 speculative chains (one per lane) started inside the segment
+    unsigned long long X[32];            // exit: first position >= segment end
+    unsigned int first[32][KFIRST];      // first positions, as offsets from seg_lo
+    unsigned int cnt[32];                // positions inside the segment
+    unsigned long long seg_lo, seg_hi, flo, fhi;
+    unsigned int geo;                    // bit0 first segment of its file, bit1 last
+    // stitching table: entry for each predecessor chain
+    unsigned int table[32];
+    // resolved state on the true chain
+    unsigned long long fin_exit;         // true exit position
+    unsigned long long fin_incl;         // boundaries up to and including this segment
+    unsigned int fin_slot;               // chain of this segment that is the true one, or NONE
+    unsigned int flagA, flagAGG, flagFIN;
+};
+
+// Stitching-table entry: count of true boundaries in the segment for that
+// entry, the chain it merges into, and two marker bits.
+constexpr uint32_t TAB_UNKNOWN = 0x80000000u;
+constexpr uint32_t TAB_CONST = 0x02000000u;  // every entry identical (first segment of a file)
+CDC_HD uint32_t tab_enc(uint32_t slot, uint32_t count) { return (slot << 26) | (count & 0x01FFFFFFu); }
+CDC_HD uint32_t tab_slot(uint32_t e) { return (e >> 26) & 31u; }
+CDC_HD uint32_t tab_count(uint32_t e) { return e & 0x01FFFFFFu; }
+
+#if defined(__CUDACC__)
+
+__device__ __forceinline__ uint32_t ld_acquire(const unsigned int* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned int* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_volatile(const unsigned int* p) {
+    return *reinterpret_cast<const volatile unsigned int*>(p);
+}
+__device__ __forceinline__ uint64_t gtimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ---- shared-memory barriers and 1-D bulk copies (TMA, no tensor map) -------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait on an mbarrier phase. Returns false when `limit_ns` passes.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t0 = gtimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (gtimer_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace cdc

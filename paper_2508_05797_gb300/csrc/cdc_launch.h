@@ -1,0 +1,77 @@
+// cdc_launch.h -- launch descriptors shared by the host API and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cdc {
+
+struct Ctrl;
+struct ItemStatus;
+
+enum SumKind { SUM_NONE = 0, SUM_MAX = 1, SUM_MAX_INV = 2, SUM_MAXP = 3 };
+
+// Stage 1 (block summaries). Positions are offsets from `base` (64-byte
+// aligned); the data is [lo, hi); reads stay inside [glo, ghi) (16-byte granules).
+struct SumLaunch {
+    const uint8_t* base;
+    uint64_t lo, hi, glo, ghi;
+    uint64_t nblk;          // blocks of 64 bytes covering [0, hi)
+    uint8_t* smax;          // per block: max (RAM/AE) or target offset / 0xFF (MAXP)
+    uint8_t* sarg;          // per block: first position of the max (RAM/AE)
+    uint32_t w;             // MAXP window
+    uint32_t halo_blocks;   // MAXP: blocks staged on each side of a tile
+    uint64_t timeout_ns;
+    Ctrl* ctrl;
+};
+
+// Stage 2 (speculative chains, stitching, resolution, output).
+struct ChainLaunch {
+    const uint8_t* base;
+    uint64_t lo, hi;
+    const uint8_t* smax;
+    const uint8_t* sarg;
+    uint64_t nblk_pad;       // summary arrays hold at least nblk_pad + 64 bytes
+    uint32_t w, mn, mx;
+    uint32_t inv;            // 0xFFFFFFFF for AE-Min (complemented bytes)
+    // files: either one stream [0, single_len) or n_files files given by
+    // file_off (logical offsets), with item_off / item_file from the batch set-up
+    const uint64_t* file_off;
+    uint64_t single_len;
+    uint64_t n_files;
+    const uint64_t* item_off;
+    const uint32_t* item_file;
+    uint64_t n_items;        // used when n_items_dev is NULL
+    const unsigned long long* n_items_dev;
+    uint64_t seg, span;
+    uint32_t win;            // summary blocks staged per segment (multiple of 16)
+    // outputs
+    uint64_t* out;
+    uint64_t capacity;
+    uint64_t* bounds_index;  // batch: n_files + 1 entries, else NULL
+    uint64_t* d_count;       // receives the total, may be NULL
+    // workspace
+    ItemStatus* st;
+    Ctrl* ctrl;
+    uint64_t timeout_ns;
+    int64_t hold_item;
+};
+
+int summary_max_smem();
+int summary_maxp_smem(uint32_t halo_blocks);
+uint32_t maxp_halo_blocks(uint32_t w);
+int summary_blocks_per_sm(int kind, uint32_t halo_blocks);
+uint64_t summary_tiles(int kind, uint64_t nblk);
+cudaError_t launch_summary(const SumLaunch& a, int kind, int grid, cudaStream_t st);
+cudaError_t launch_reset(Ctrl* ctrl, cudaStream_t st);
+
+int chain_smem(int rule, uint32_t win);
+int chain_blocks_per_sm(int rule, uint32_t win);
+cudaError_t launch_chain(const ChainLaunch& a, int rule, int grid, cudaStream_t st);
+
+// batch set-up: item_off (n_files + 1), item_file, ctrl->n_items
+cudaError_t launch_batch_setup(const uint64_t* file_off, uint64_t n_files, uint64_t seg, uint64_t* item_off,
+                               uint32_t* item_file, uint64_t* scan_tmp, Ctrl* ctrl, cudaStream_t st,
+                               int* launches);
+uint64_t batch_scan_tmp_elems(uint64_t n_files);
+
+}  // namespace cdc

@@ -1,0 +1,471 @@
+// chain_logic.cuh -- per-thread chunk rules over block summaries (RAM, AE, MAXP).
+//
+// next(s) returns the end of the chunk that starts at s, exactly as the
+// sequential rules of arxiv 2508.05797 define it (Section 2.1, Section 3.3;
+// the min / max rule of Section 2.1). What makes it fast is where it looks:
+// instead of every byte it reads per-64-byte-block summaries written by the
+// summary kernel, and touches raw bytes only where a summary cannot decide.
+//
+//   * Extreme Byte Search (Section 3.1) over a window becomes a max over the
+//     block maxima of the whole blocks inside it (4 blocks per 32-bit word,
+//     combined with byte-wise SIMD max), plus raw reads of the partial end
+//     blocks only when their block maximum could raise the result.
+//   * Range Scan (Section 3.2) for the first byte >= M becomes a packed
+//     compare over the block maxima (4 per word); in the hit block the first
+//     occurrence of the block maximum is the answer when that maximum equals
+//     M, otherwise the block's bytes are scanned.
+//   * AE walks its targets block by block: inside a block every target but
+//     the last has its next greater byte within 63 bytes, so with w >= 64
+//     none of them can end a chunk, and the walk jumps to the block's first
+//     maximum.
+//   * MAXP reads the target found by the summary kernel in each block (at
+//     most one per block when w >= 63) and keeps the first one that fits
+//     the chunk-size rules.
+//
+// Positions are byte offsets from a 64-byte aligned base ("physical"); a
+// file occupies [flo, fhi). Every function is __host__ __device__ so that the
+// same code can be checked on the CPU.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define CDC_HD __host__ __device__ __forceinline__
+#else
+#define CDC_HD inline
+#endif
+
+namespace cdc {
+
+constexpr uint32_t NONE_SLOT = 0xFFu;
+
+CDC_HD uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+CDC_HD uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+// ---- byte-wise SIMD helpers (device intrinsics; portable fallbacks on the host)
+CDC_HD uint32_t vmax4(uint32_t a, uint32_t b) {
+#if defined(__CUDA_ARCH__)
+    return __vmaxu4(a, b);
+#else
+    uint32_t r = 0;
+    for (int k = 0; k < 4; k++) {
+        uint32_t x = (a >> (8 * k)) & 0xFFu, y = (b >> (8 * k)) & 0xFFu;
+        r |= (x > y ? x : y) << (8 * k);
+    }
+    return r;
+#endif
+}
+
+// 0xFF in each byte where a >= b (unsigned)
+CDC_HD uint32_t vcmpge4(uint32_t a, uint32_t b) {
+#if defined(__CUDA_ARCH__)
+    return __vcmpgeu4(a, b);
+#else
+    uint32_t r = 0;
+    for (int k = 0; k < 4; k++)
+        if (((a >> (8 * k)) & 0xFFu) >= ((b >> (8 * k)) & 0xFFu)) r |= 0xFFu << (8 * k);
+    return r;
+#endif
+}
+
+CDC_HD uint32_t vcmpeq4(uint32_t a, uint32_t b) {
+#if defined(__CUDA_ARCH__)
+    return __vcmpeq4(a, b);
+#else
+    uint32_t r = 0;
+    for (int k = 0; k < 4; k++)
+        if (((a >> (8 * k)) & 0xFFu) == ((b >> (8 * k)) & 0xFFu)) r |= 0xFFu << (8 * k);
+    return r;
+#endif
+}
+
+CDC_HD int ffs32(uint32_t x) {
+#if defined(__CUDA_ARCH__)
+    return __ffs((int)x);
+#else
+    return __builtin_ffs((int)x);
+#endif
+}
+
+// largest byte of a word
+CDC_HD uint32_t hmax4(uint32_t v) {
+    v = vmax4(v, v >> 16);
+    v = vmax4(v, v >> 8);
+    return v & 0xFFu;
+}
+
+// keep the bytes of word `wi` (bytes [4wi, 4wi+4)) that lie in [a, b)
+CDC_HD uint32_t clip_word(uint32_t v, uint64_t wi, uint64_t a, uint64_t b) {
+    uint64_t lo = wi << 2;
+    if (lo < a) v &= 0xFFFFFFFFu << (8 * (uint32_t)(a - lo));
+    if (lo + 4 > b) v &= 0xFFFFFFFFu >> (8 * (uint32_t)(lo + 4 - b));
+    return v;
+}
+
+// ---- data views ------------------------------------------------------------
+
+// Raw bytes of the input. `inv` = 0xFFFFFFFF reads 255 - b (AE-Min runs the
+// AE-Max rules on complemented bytes). Callers only read words holding at
+// least one byte of [flo, fhi), which lie inside the buffer's 16-byte granules.
+struct RawView {
+    const uint8_t* base;
+    uint32_t inv;
+    CDC_HD uint32_t word(uint64_t wi) const {
+#if defined(__CUDA_ARCH__)
+        return __ldg(reinterpret_cast<const uint32_t*>(base) + wi) ^ inv;
+#else
+        return reinterpret_cast<const uint32_t*>(base)[wi] ^ inv;
+#endif
+    }
+    CDC_HD uint32_t byte(uint64_t p) const { return (word(p >> 2) >> (8 * (uint32_t)(p & 3))) & 0xFFu; }
+};
+
+// Per-block summaries: m[b] (block maximum, or for MAXP the offset of the
+// block's target / 0xFF) and a[b] (offset of the first maximum). A window of
+// blocks [wb0, wb0 + wn) may be staged in fast memory (sm, sa); other blocks
+// are read from the global arrays (gm, ga). wb0 is a multiple of 16.
+struct SumView {
+    const uint8_t* gm;
+    const uint8_t* ga;
+    const uint8_t* sm;
+    const uint8_t* sa;
+    uint64_t wb0, wn;
+    CDC_HD uint32_t m(uint64_t b) const {
+        uint64_t r = b - wb0;
+        return (b >= wb0 && r < wn) ? sm[r] : gm[b];
+    }
+    CDC_HD uint32_t a(uint64_t b) const {
+        uint64_t r = b - wb0;
+        return (b >= wb0 && r < wn) ? sa[r] : ga[b];
+    }
+    // m[] of blocks [4wi, 4wi + 4) as one little-endian word
+    CDC_HD uint32_t m4(uint64_t wi) const {
+        uint64_t b = wi << 2, r = b - wb0;
+        if (b >= wb0 && r + 4 <= wn) return *reinterpret_cast<const uint32_t*>(sm + r);
+        return *reinterpret_cast<const uint32_t*>(gm + b);
+    }
+};
+
+struct Prm {
+    uint32_t w, mn, mx;
+};
+
+// ---- raw helpers (bytes [a, b), a < b) --------------------------------------
+
+CDC_HD uint32_t raw_max(const RawView& R, uint64_t a, uint64_t b) {
+    uint32_t acc = 0;
+    for (uint64_t wi = a >> 2, we = (b + 3) >> 2; wi < we; wi++)
+        acc = vmax4(acc, clip_word(R.word(wi), wi, a, b));
+    return hmax4(acc);
+}
+
+// maximum of [a, b) and the position of its first occurrence
+CDC_HD void raw_max_first(const RawView& R, uint64_t a, uint64_t b, uint32_t* v, uint64_t* p) {
+    uint32_t M = raw_max(R, a, b);
+    uint32_t Mx = M * 0x01010101u;
+    for (uint64_t wi = a >> 2, we = (b + 3) >> 2; wi < we; wi++) {
+        uint32_t e = clip_word(vcmpeq4(R.word(wi), Mx), wi, a, b);
+        if (e) {
+            *v = M;
+            *p = (wi << 2) + (uint32_t)((ffs32(e) - 1) >> 3);
+            return;
+        }
+    }
+    *v = M;
+    *p = a;  // unreachable: M occurs in [a, b)
+}
+
+// first position in [a, b) whose byte is >= M (M >= 1); b if none
+CDC_HD uint64_t raw_first_geq(const RawView& R, uint64_t a, uint64_t b, uint32_t M, uint32_t* val) {
+    uint32_t Mx = M * 0x01010101u;
+    for (uint64_t wi = a >> 2, we = (b + 3) >> 2; wi < we; wi++) {
+        uint32_t v = R.word(wi);
+        uint32_t h = clip_word(vcmpge4(v, Mx), wi, a, b);
+        if (h) {
+            uint32_t k = (uint32_t)((ffs32(h) - 1) >> 3);
+            *val = (v >> (8 * k)) & 0xFFu;
+            return (wi << 2) + k;
+        }
+    }
+    return b;
+}
+
+// ---- summary helpers --------------------------------------------------------
+
+// maximum of m[] over blocks [b0, b1), b0 < b1
+CDC_HD uint32_t sum_max(const SumView& S, uint64_t b0, uint64_t b1) {
+    uint32_t acc = 0;
+    for (uint64_t wi = b0 >> 2, we = (b1 + 3) >> 2; wi < we; wi++) {
+        acc = vmax4(acc, clip_word(S.m4(wi), wi, b0, b1));
+        if (acc == 0xFFFFFFFFu) break;  // cannot grow further
+    }
+    return hmax4(acc);
+}
+
+// first block in [b0, b1) with m[] >= M (M >= 1); b1 if none
+CDC_HD uint64_t sum_first_geq(const SumView& S, uint64_t b0, uint64_t b1, uint32_t M) {
+    uint32_t Mx = M * 0x01010101u;
+    for (uint64_t wi = b0 >> 2, we = (b1 + 3) >> 2; wi < we; wi++) {
+        uint32_t h = clip_word(vcmpge4(S.m4(wi), Mx), wi, b0, b1);
+        if (h) return (wi << 2) + (uint32_t)((ffs32(h) - 1) >> 3);
+    }
+    return b1;
+}
+
+// Extreme Byte Search: maximum byte of [a, b), a < b
+CDC_HD uint32_t range_max(const SumView& S, const RawView& R, uint64_t a, uint64_t b) {
+    uint64_t ba = a >> 6, bl = (b - 1) >> 6;
+    if (ba == bl) {
+        if ((a & 63) == 0 && (b & 63) == 0) return S.m(ba);
+        if (S.m(ba) == 0) return 0;
+        return raw_max(R, a, b);
+    }
+    uint64_t fb = (a + 63) >> 6, lb = b >> 6;  // whole blocks [fb, lb)
+    uint32_t M = fb < lb ? sum_max(S, fb, lb) : 0;
+    if ((a & 63) && S.m(ba) > M) {
+        uint32_t h = raw_max(R, a, (ba + 1) << 6);
+        if (h > M) M = h;
+    }
+    if ((b & 63) && S.m(bl) > M) {
+        uint32_t t = raw_max(R, bl << 6, b);
+        if (t > M) M = t;
+    }
+    return M;
+}
+
+// Range Scan (GEQ): first position in [from, to) with byte >= M (M >= 1);
+// `to` if none. *val receives the byte found.
+CDC_HD uint64_t first_geq(const SumView& S, const RawView& R, uint64_t from, uint64_t to,
+                          uint32_t M, uint32_t* val) {
+    uint64_t b = from >> 6;
+    uint64_t bend = (to - 1) >> 6;  // last block touched
+    if ((from & 63) != 0 || b == bend) {
+        uint64_t bhi = (b + 1) << 6;
+        uint32_t bm = S.m(b);
+        if (bm >= M) {
+            uint64_t a = (b << 6) + S.a(b);
+            if (bm == M && a >= from) {
+                // every byte >= M in this block equals M; the first is a
+                if (a < to) { *val = M; return a; }
+                return to;  // a >= to implies to <= bhi
+            }
+            uint64_t e = umin64(bhi, to);
+            uint64_t r = raw_first_geq(R, from, e, M, val);
+            if (r < e) return r;
+        }
+        if (b == bend) return to;
+        b++;
+    }
+    while (b <= bend) {
+        uint64_t bh = sum_first_geq(S, b, bend + 1, M);
+        if (bh > bend) return to;
+        uint64_t blo = bh << 6;
+        uint32_t bm = S.m(bh);
+        uint64_t a = blo + S.a(bh);
+        if (bm == M) {
+            if (a < to) { *val = M; return a; }
+            return to;
+        }
+        uint64_t e = umin64(blo + 64, to);
+        uint64_t r = raw_first_geq(R, blo, e, M, val);
+        if (r < e) return r;
+        if (e == to) return to;
+        b = bh + 1;
+    }
+    return to;
+}
+
+// ---- the chunk rules ---------------------------------------------------------
+
+// RAM (Section 2.1, Section 3.3).
+CDC_HD uint64_t next_ram(const SumView& S, const RawView& R, const Prm& P, uint64_t fhi,
+                         uint64_t s) {
+    if (fhi - s <= P.w) return fhi;
+    uint64_t limit = umin64(fhi, s + P.mx);
+    uint64_t t = s + P.w;
+    uint32_t M = range_max(S, R, s, t);
+    uint64_t j0 = umax64(t, s + P.mn - 1);
+    if (j0 >= limit) return limit;
+    if (M == 0) return j0 + 1;
+    uint32_t val;
+    uint64_t j = first_geq(S, R, j0, limit, M, &val);
+    return j < limit ? j + 1 : limit;
+}
+
+// AE-Max over the (possibly complemented) bytes, w >= 64 (Section 2.1,
+// Section 3.3). p is the current target, v its value, cur the first byte not
+// yet known to be <= v.
+CDC_HD uint64_t next_ae(const SumView& S, const RawView& R, const Prm& P, uint64_t fhi,
+                        uint64_t s) {
+    uint64_t limit = umin64(fhi, s + P.mx);
+    if (s + 1 >= limit) return limit;
+    uint64_t p;
+    uint32_t v;
+    {
+        uint64_t b = s >> 6;
+        uint64_t a = (b << 6) + S.a(b);
+        if (a >= s && a < limit) {
+            p = a;
+            v = S.m(b);
+        } else {
+            raw_max_first(R, s, umin64((b + 1) << 6, limit), &v, &p);
+        }
+    }
+    uint64_t cur = p + 1;
+    for (;;) {
+        uint64_t t = umax64(p + P.w, s + P.mn - 1);
+        if (t >= limit) return limit;
+        if (v == 255) return t + 1;
+        uint64_t to = t + 1;
+        if (cur & 63) {
+            uint64_t bc = cur >> 6, bhi = (bc + 1) << 6;
+            uint32_t bm = S.m(bc);
+            if (bm > v) {
+                uint64_t a = (bc << 6) + S.a(bc);
+                if (a >= cur && bhi <= to) {
+                    p = a; v = bm; cur = a + 1;
+                    continue;
+                }
+                uint64_t e = umin64(bhi, to);
+                uint32_t val;
+                uint64_t q = raw_first_geq(R, cur, e, v + 1, &val);
+                if (q < e) {
+                    p = q; v = val; cur = q + 1;
+                    continue;
+                }
+            }
+            if (bhi >= to) return to;
+            cur = bhi;
+        }
+        uint64_t bf = cur >> 6, bl = (to - 1) >> 6;
+        uint64_t bh = sum_first_geq(S, bf, bl + 1, v + 1);
+        if (bh > bl) return to;
+        uint64_t blo = bh << 6;
+        if (blo + 64 <= to) {
+            p = blo + S.a(bh); v = S.m(bh); cur = p + 1;
+            continue;
+        }
+        uint32_t val;
+        uint64_t q = raw_first_geq(R, blo, to, v + 1, &val);
+        if (q < to) {
+            p = q; v = val; cur = q + 1;
+            continue;
+        }
+        return to;
+    }
+}
+
+// MAXP from per-block targets (w >= 63: at most one target per block).
+// Only targets whose windows lie inside the file [flo, fhi) count.
+CDC_HD uint64_t next_maxp(const SumView& S, const Prm& P, uint64_t flo, uint64_t fhi,
+                          uint64_t s) {
+    uint64_t limit = umin64(fhi, s + P.mx);
+    uint64_t cmin = umax64(s + P.mn - 1, flo + P.w);
+    uint64_t cend = fhi > flo + P.w ? umin64(limit, fhi - P.w) : 0;
+    if (cmin >= cend) return limit;
+    uint64_t b0 = cmin >> 6, b1 = ((cend - 1) >> 6) + 1;
+    for (uint64_t wi = b0 >> 2, we = (b1 + 3) >> 2; wi < we; wi++) {
+        uint32_t v = S.m4(wi);
+        if (v == 0xFFFFFFFFu) continue;
+        for (uint32_t k = 0; k < 4; k++) {
+            uint64_t bb = (wi << 2) + k;
+            uint32_t o = (v >> (8 * k)) & 0xFFu;
+            if (o == 0xFFu || bb < b0 || bb >= b1) continue;
+            uint64_t c = (bb << 6) + o;
+            if (c >= cmin && c < cend) return c + 1;
+        }
+    }
+    return limit;
+}
+
+// ---- byte-level rules (no summaries): used for w below the block size and
+// for cross-checking the summary path -------------------------------------------
+
+CDC_HD uint64_t next_ram_bytes(const RawView& R, const Prm& P, uint64_t fhi, uint64_t s) {
+    if (fhi - s <= P.w) return fhi;
+    uint64_t limit = umin64(fhi, s + P.mx);
+    uint64_t t = s + P.w;
+    uint32_t M = raw_max(R, s, t);
+    uint64_t j0 = umax64(t, s + P.mn - 1);
+    if (j0 >= limit) return limit;
+    if (M == 0) return j0 + 1;
+    uint32_t val;
+    uint64_t j = raw_first_geq(R, j0, limit, M, &val);
+    return j < limit ? j + 1 : limit;
+}
+
+CDC_HD uint64_t next_ae_bytes(const RawView& R, const Prm& P, uint64_t fhi, uint64_t s) {
+    uint64_t limit = umin64(fhi, s + P.mx);
+    uint64_t p = s;
+    uint32_t v = R.byte(s);
+    uint64_t cur = s + 1;
+    for (;;) {
+        uint64_t t = umax64(p + P.w, s + P.mn - 1);
+        if (t >= limit) return limit;
+        if (v == 255) return t + 1;
+        uint32_t val;
+        uint64_t q = raw_first_geq(R, cur, t + 1, v + 1, &val);
+        if (q > t) return t + 1;
+        p = q; v = val; cur = q + 1;
+    }
+}
+
+CDC_HD bool maxp_target_bytes(const RawView& R, uint64_t c, uint32_t w) {
+    uint32_t v = R.byte(c);
+    if (v == 0) return false;
+    uint32_t lm = raw_max(R, c - w, c);
+    if (lm >= v) return false;
+    return raw_max(R, c + 1, c + 1 + w) < v;
+}
+
+CDC_HD uint64_t next_maxp_bytes(const RawView& R, const Prm& P, uint64_t flo, uint64_t fhi,
+                                uint64_t s) {
+    uint64_t limit = umin64(fhi, s + P.mx);
+    uint64_t cmin = umax64(s + P.mn - 1, flo + P.w);
+    uint64_t cend = fhi > flo + P.w ? umin64(limit, fhi - P.w) : 0;
+    for (uint64_t c = cmin; c < cend; c++)
+        if (maxp_target_bytes(R, c, P.w)) return c + 1;
+    return limit;
+}
+
+// Which rule the chain stage runs.
+enum Rule : int {
+    RULE_RAM = 0,        // RAM over summaries
+    RULE_AE = 1,         // AE over summaries (w >= 64)
+    RULE_MAXP = 2,       // MAXP over per-block targets (w >= 63)
+    RULE_RAM_BYTES = 3,
+    RULE_AE_BYTES = 4,
+    RULE_MAXP_BYTES = 5
+};
+
+template <int RULE>
+CDC_HD uint64_t next_cut(const SumView& S, const RawView& R, const Prm& P, uint64_t flo,
+                         uint64_t fhi, uint64_t s) {
+    if (RULE == RULE_RAM) return next_ram(S, R, P, fhi, s);
+    if (RULE == RULE_AE) return next_ae(S, R, P, fhi, s);
+    if (RULE == RULE_MAXP) return next_maxp(S, P, flo, fhi, s);
+    if (RULE == RULE_RAM_BYTES) return next_ram_bytes(R, P, fhi, s);
+    if (RULE == RULE_AE_BYTES) return next_ae_bytes(R, P, fhi, s);
+    return next_maxp_bytes(R, P, flo, fhi, s);
+}
+
+// ---- block summaries (the summary kernel's per-block arithmetic, also used
+// by the host check) ------------------------------------------------------------
+
+// maximum and first position of the maximum of 64 bytes given as 16 words
+CDC_HD void block_max_first(const uint32_t* wds, uint32_t* mx, uint32_t* first) {
+    uint32_t acc = 0;
+    for (int i = 0; i < 16; i++) acc = vmax4(acc, wds[i]);
+    uint32_t M = hmax4(acc), Mx = M * 0x01010101u;
+    for (int i = 0; i < 16; i++) {
+        uint32_t e = vcmpeq4(wds[i], Mx);
+        if (e) {
+            *mx = M;
+            *first = (uint32_t)(4 * i + ((ffs32(e) - 1) >> 3));
+            return;
+        }
+    }
+    *mx = M;
+    *first = 0;
+}
+
+}  // namespace cdc
