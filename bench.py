@@ -43,10 +43,10 @@ def wtable():
         return json.load(f)
 
 
-def configs():
+def configs(algs=ALGS, means=MEANS):
     t = wtable()["mixed_4g_seed1"]
     return [(alg, mean, t[alg][str(mean)]["w"], t[alg][str(mean)]["min"], t[alg][str(mean)]["max"])
-            for alg in ALGS for mean in MEANS]
+            for alg in algs for mean in means]
 
 
 def peaks():
@@ -218,6 +218,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--algs", default=",".join(ALGS), help="subset of ram,ae,maxp (profiling cases)")
+    ap.add_argument("--means", default=",".join(map(str, MEANS)), help="subset of 4096,8192,16384")
+    ap.add_argument("--len-mib", type=int, default=STREAM_LEN // MIB,
+                    help="stream length (a prefix of the 4 GiB stream; profiling cases)")
     args = ap.parse_args()
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
@@ -233,16 +237,18 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     seed = 1 + rank
-    host = torch.empty(STREAM_LEN, dtype=torch.uint8, pin_memory=True)
-    synth.mixed_range(seed, STREAM_LEN, 0, STREAM_LEN, out=host.numpy())
+    n = args.len_mib * MIB
+    host = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    synth.mixed_range(seed, STREAM_LEN, 0, n, out=host.numpy())
     data = host.to(dev, non_blocking=False)
-    cfg = configs()
+    cfg = configs(tuple(args.algs.split(",")), tuple(int(x) for x in args.means.split(",")))
+    ncfg = len(cfg)
     handles, outs, counts = [], [], []
     for alg, mean, w, mn, mx in cfg:
         ck = Chunker(local)
-        ck.reserve(alg, w, mn, mx, STREAM_LEN)
+        ck.reserve(alg, w, mn, mx, n)
         handles.append(ck)
-        outs.append(torch.empty(STREAM_LEN // mn + 1, dtype=torch.int64, device=dev))
+        outs.append(torch.empty(n // mn + 1, dtype=torch.int64, device=dev))
         counts.append(torch.zeros(1, dtype=torch.int64, device=dev))
     stream = torch.cuda.current_stream(dev)
 
@@ -282,39 +288,43 @@ def main():
         sum_ms_total += sms
         per_cfg.append({"alg": alg, "mean": mean, "w": w, "calls": calls, "summary_ms": sms / max(calls, 1),
                         "chain_ms": cms / max(calls, 1), "boundaries": int(c.item())})
-    total_bytes = 9 * STREAM_LEN * args.steps * world
+    total_bytes = ncfg * n * args.steps * world
     gbs = total_bytes / (ms / 1e3) / 1e9
     peak, peak_kind = peaks()
     per_alg = {}
     for alg in ALGS:
         rows = [r for r in per_cfg if r["alg"] == alg]
         t = sum(r["summary_ms"] + r["chain_ms"] for r in rows)
-        per_alg[alg] = {"GBps": round(len(rows) * STREAM_LEN / (t / 1e3) / 1e9, 1),
-                        "hbm_frac": round(len(rows) * STREAM_LEN / (t / 1e3) / 1e9 / peak, 4),
+        if not rows:
+            continue
+        per_alg[alg] = {"GBps": round(len(rows) * n / (t / 1e3) / 1e9, 1),
+                        "hbm_frac": round(len(rows) * n / (t / 1e3) / 1e9 / peak, 4),
                         "summary_ms": [round(r["summary_ms"], 4) for r in rows],
                         "chain_ms": [round(r["chain_ms"], 4) for r in rows]}
     # roofline of the dominant kernel (block summaries: reads every input byte once)
-    summ_avg_ms = sum_ms_total / max(1, 9 * args.steps)
-    achieved = STREAM_LEN / (summ_avg_ms / 1e3) / 1e9
+    summ_avg_ms = sum_ms_total / max(1, ncfg * args.steps)
+    achieved = n / (summ_avg_ms / 1e3) / 1e9
     prof, _ = profile_traffic()
     traffic = None
     if prof:
-        traffic = int(prof["dram_bytes_per_input_byte"] * STREAM_LEN)
+        traffic = int(prof["dram_bytes_per_input_byte"] * n)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
                 "kernel": "k_summary_max / k_summary_maxp (stage 1, block summaries)",
-                "algorithmic_bytes_per_launch": STREAM_LEN}
+                "algorithmic_bytes_per_launch": n}
     line = {"metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded)",
-            "config": {"workload": WORKLOAD, "bytes_per_step": 9 * STREAM_LEN,
+            "config": {"workload": WORKLOAD if ncfg == 9 and n == STREAM_LEN else
+                       "%s; subset algs=%s means=%s, first %d MiB" % (WORKLOAD, args.algs, args.means, args.len_mib),
+                       "bytes_per_step": ncfg * n,
                        "l2": "inputs larger than L2 (4 GiB per call, 129 MB L2)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_frac": round(gbs / world / peak, 4), "per_alg": per_alg, "roofline": roofline,
             "gpu_launches": int(launches), "clocks": clocks}
     # end to end through the host entry point (pinned host memory in, host boundaries out)
     if not args.no_e2e:
-        outs_h = [np.empty(STREAM_LEN // mn + 1, dtype=np.uint64) for (_, _, _, mn, _) in cfg]
+        outs_h = [np.empty(n // mn + 1, dtype=np.uint64) for (_, _, _, mn, _) in cfg]
         hnp = host.numpy()
         d2h = 0
         torch.cuda.synchronize()
@@ -328,8 +338,8 @@ def main():
                 d2h += b.size * 8
         torch.cuda.synchronize()
         dt = allreduce_max(time.perf_counter() - t0, world)
-        line["e2e"] = {"value": round(9 * STREAM_LEN * e2e_steps * world / dt / 1e9, 2), "unit": "GB/s",
-                       "h2d_bytes_per_step": 9 * STREAM_LEN, "d2h_bytes_per_step": int(d2h),
+        line["e2e"] = {"value": round(ncfg * n * e2e_steps * world / dt / 1e9, 2), "unit": "GB/s",
+                       "h2d_bytes_per_step": ncfg * n, "d2h_bytes_per_step": int(d2h),
                        "steps": e2e_steps}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

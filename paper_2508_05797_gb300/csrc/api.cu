@@ -19,8 +19,12 @@ struct cdc_handle_s {
     uint8_t* sarg = nullptr;
     size_t sum_cap = 0;  // bytes of smax
     size_t sarg_cap = 0;
-    ItemStatus* st = nullptr;
-    size_t st_cap = 0;   // items
+    uint8_t* ssup = nullptr;
+    size_t ssup_cap = 0;
+    uint8_t* st = nullptr;  // SegState array
+    size_t st_cap = 0;      // bytes
+    uint8_t* groups = nullptr;  // GroupState array
+    size_t groups_cap = 0;      // bytes
     Ctrl* ctrl = nullptr;
     uint64_t* item_off = nullptr;
     uint64_t* scan_tmp = nullptr;
@@ -116,6 +120,8 @@ extern "C" cdc_status cdc_destroy(cdc_handle h) {
     cudaDeviceSynchronize();
     cudaFree(h->smax);
     cudaFree(h->sarg);
+    cudaFree(h->ssup);
+    cudaFree(h->groups);
     cudaFree(h->st);
     cudaFree(h->ctrl);
     cudaFree(h->item_off);
@@ -251,7 +257,7 @@ static uint32_t pick_win(cdc_params p, uint64_t seg) {
 
 struct Geo {
     const uint8_t* base;
-    uint64_t lo, hi, glo, ghi, nblk, nblk_pad;
+    uint64_t lo, hi, glo, ghi, nblk, nblk_pad, nsup;
 };
 
 static Geo geometry(const uint8_t* data, uint64_t len) {
@@ -264,6 +270,7 @@ static Geo geometry(const uint8_t* data, uint64_t len) {
     g.ghi = (g.hi + 15) & ~15ull;
     g.nblk = (g.hi + 63) / 64;
     g.nblk_pad = (g.nblk + 15) & ~15ull;
+    g.nsup = (g.hi + 4095) / 4096;
     return g;
 }
 
@@ -282,8 +289,12 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
         const size_t need = g.nblk_pad + 64;
         if ((s = grow(&h->smax, &h->sum_cap, need, false, st)) != CDC_OK) return s;
         if (pl.sum != SUM_MAXP && (s = grow(&h->sarg, &h->sarg_cap, need, false, st)) != CDC_OK) return s;
+        if ((s = grow(&h->ssup, &h->ssup_cap, g.nsup + 64, false, st)) != CDC_OK) return s;
     }
-    if ((s = grow(&h->st, &h->st_cap, items, true, st)) != CDC_OK) return s;
+    if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, st)) != CDC_OK) return s;
+    if ((s = grow(&h->groups, &h->groups_cap, ((items + GS - 1) / GS + 1) * group_state_bytes(), false, st)) !=
+        CDC_OK)
+        return s;
     if (batch) {
         if ((s = grow(&h->item_off, &h->files_cap, n_files + 1, false, st)) != CDC_OK) return s;
         if ((s = grow(&h->scan_tmp, &h->scan_cap, batch_scan_tmp_elems(n_files), false, st)) != CDC_OK) return s;
@@ -308,6 +319,8 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
         a.nblk = g.nblk;
         a.smax = h->smax;
         a.sarg = h->sarg;
+        a.ssup = h->ssup;
+        a.nsup = g.nsup;
         a.w = p.w;
         a.halo_blocks = pl.halo;
         a.timeout_ns = timeout_ns;
@@ -329,6 +342,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     c.hi = g.hi;
     c.smax = h->smax;
     c.sarg = h->sarg ? h->sarg : h->smax;
+    c.ssup = h->ssup;
     c.nblk_pad = g.nblk_pad;
     c.w = p.w; c.mn = p.min; c.mx = p.max;
     c.inv = pl.inv;
@@ -346,15 +360,28 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     c.capacity = capacity;
     c.bounds_index = bounds_index;
     c.d_count = d_count;
-    c.st = h->st;
+    c.st = reinterpret_cast<SegState*>(h->st);
+    c.groups = h->groups;
     c.ctrl = h->ctrl;
     c.timeout_ns = timeout_ns;
     c.hold_item = h->hold_item;
-    uint64_t grid = (uint64_t)h->sm_count * chain_blocks_per_sm(pl.rule, c.win);
-    if (grid > items) grid = items;
-    if (grid < 1) grid = 1;
-    if (launch_chain(c, pl.rule, (int)grid, st) != cudaSuccess) return CDC_ERR_CUDA;
-    h->launches++;
+    if (pl.sum != SUM_NONE) {
+        const uint64_t mx4k = ((uint64_t)p.max + 4095) & ~4095ull;
+        c.quiet_run = pl.sum == SUM_MAXP ? (uint32_t)(p.max / 8192 > 1 ? p.max / 8192 : 1) : 1u;
+        c.adj_before = ((mx4k / 4) + 4095) & ~4095ull;
+        c.adj_after = mx4k;
+        c.adj_cap = 64ull << 20;
+    }
+    ChainGrids gr;
+    const uint64_t ngroups = (items + GS - 1) / GS;
+    uint64_t gs = (uint64_t)h->sm_count * spec_blocks_per_sm(pl.rule, c.win);
+    gr.spec = (int)(gs < items ? gs : items);
+    gr.groups = (int)(ngroups < (uint64_t)h->sm_count * 16 ? ngroups : (uint64_t)h->sm_count * 16);
+    gr.output = (int)(items < (uint64_t)h->sm_count * 32 ? items : (uint64_t)h->sm_count * 32);
+    if (gr.spec < 1) gr.spec = 1;
+    if (gr.groups < 1) gr.groups = 1;
+    if (gr.output < 1) gr.output = 1;
+    if (launch_chain(c, pl.rule, gr, st, &h->launches) != cudaSuccess) return CDC_ERR_CUDA;
     if (rec) {
         cudaEventRecord(ev[2], st);
         h->last_ev = ev;
@@ -481,7 +508,11 @@ extern "C" cdc_status cdc_reserve(cdc_handle h, cdc_alg alg, cdc_params p, size_
         if ((s = grow(&h->smax, &h->sum_cap, nblk_pad + 64, false, 0)) != CDC_OK) return s;
         if (pl.sum != SUM_MAXP && (s = grow(&h->sarg, &h->sarg_cap, nblk_pad + 64, false, 0)) != CDC_OK) return s;
     }
-    if ((s = grow(&h->st, &h->st_cap, items, true, 0)) != CDC_OK) return s;
+    if (pl.sum != SUM_NONE && (s = grow(&h->ssup, &h->ssup_cap, len / 4096 + 66, false, 0)) != CDC_OK) return s;
+    if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, 0)) != CDC_OK) return s;
+    if ((s = grow(&h->groups, &h->groups_cap, ((items + GS - 1) / GS + 1) * group_state_bytes(), false, 0)) !=
+        CDC_OK)
+        return s;
     if (n_files) {
         if ((s = grow(&h->item_off, &h->files_cap, n_files + 1, false, 0)) != CDC_OK) return s;
         if ((s = grow(&h->scan_tmp, &h->scan_cap, batch_scan_tmp_elems(n_files), false, 0)) != CDC_OK) return s;

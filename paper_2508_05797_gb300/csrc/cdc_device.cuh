@@ -8,7 +8,7 @@
 namespace cdc {
 
 constexpr uint32_t FULL = 0xFFFFFFFFu;
-constexpr int KFIRST = 8;  // chain positions per lane kept for stitching
+constexpr int KF = 8;  // positions per chain kept for stitching
 
 // Control block of a handle (device memory, one per handle).
 struct Ctrl {
@@ -22,31 +22,10 @@ struct Ctrl {
 };
 enum : unsigned int { ERR_TIMEOUT = 1u, ERR_INTERNAL = 2u };
 
-// Published state of one segment ("item"). Flags hold the epoch of the
-// launch that set them, so stale state from an earlier launch never matches.
-struct __align__(128) ItemStatus {
-    // phase A: 32 speculative chains (one per lane) started inside the segment
-    unsigned long long X[32];            // exit: first position >= segment end
-    unsigned int first[32][KFIRST];      // first positions, as offsets from seg_lo
-    unsigned int cnt[32];                // positions inside the segment
-    unsigned long long seg_lo, seg_hi, flo, fhi;
-    unsigned int geo;                    // bit0 first segment of its file, bit1 last
-    // stitching table: entry for each predecessor chain
-    unsigned int table[32];
-    // resolved state on the true chain
-    unsigned long long fin_exit;         // true exit position
-    unsigned long long fin_incl;         // boundaries up to and including this segment
-    unsigned int fin_slot;               // chain of this segment that is the true one, or NONE
-    unsigned int flagA, flagAGG, flagFIN;
-};
-
-// Stitching-table entry: count of true boundaries in the segment for that
-// entry, the chain it merges into, and two marker bits.
-constexpr uint32_t TAB_UNKNOWN = 0x80000000u;
-constexpr uint32_t TAB_CONST = 0x02000000u;  // every entry identical (first segment of a file)
-CDC_HD uint32_t tab_enc(uint32_t slot, uint32_t count) { return (slot << 26) | (count & 0x01FFFFFFu); }
-CDC_HD uint32_t tab_slot(uint32_t e) { return (e >> 26) & 31u; }
-CDC_HD uint32_t tab_count(uint32_t e) { return e & 0x01FFFFFFu; }
+// Speculation geometry of the chain stage.
+constexpr int NW = 4;            // warps per segment
+constexpr int NL = 32 * NW;      // speculative chains per segment
+constexpr int GS = 128;          // segments per group in the table scan
 
 #if defined(__CUDACC__)
 

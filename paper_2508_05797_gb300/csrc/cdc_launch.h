@@ -6,7 +6,7 @@
 namespace cdc {
 
 struct Ctrl;
-struct ItemStatus;
+struct SegState;
 
 enum SumKind { SUM_NONE = 0, SUM_MAX = 1, SUM_MAX_INV = 2, SUM_MAXP = 3 };
 
@@ -18,6 +18,8 @@ struct SumLaunch {
     uint64_t nblk;          // blocks of 64 bytes covering [0, hi)
     uint8_t* smax;          // per block: max (RAM/AE) or target offset / 0xFF (MAXP)
     uint8_t* sarg;          // per block: first position of the max (RAM/AE)
+    uint8_t* ssup;          // per 4 KiB superblock: max byte (RAM/AE) or target count (MAXP)
+    uint64_t nsup;          // superblocks covering [0, hi)
     uint32_t w;             // MAXP window
     uint32_t halo_blocks;   // MAXP: blocks staged on each side of a tile
     uint64_t timeout_ns;
@@ -30,6 +32,7 @@ struct ChainLaunch {
     uint64_t lo, hi;
     const uint8_t* smax;
     const uint8_t* sarg;
+    const uint8_t* ssup;     // 4 KiB superblock summaries (quiet-region detection)
     uint64_t nblk_pad;       // summary arrays hold at least nblk_pad + 64 bytes
     uint32_t w, mn, mx;
     uint32_t inv;            // 0xFFFFFFFF for AE-Min (complemented bytes)
@@ -44,13 +47,19 @@ struct ChainLaunch {
     const unsigned long long* n_items_dev;
     uint64_t seg, span;
     uint32_t win;            // summary blocks staged per segment (multiple of 16)
+    // segment bounds move out of quiet regions: runs of quiet_run quiet
+    // superblocks (0 = never move) within [y - adj_before, y + adj_after);
+    // a bound moves at most adj_cap bytes
+    uint32_t quiet_run;
+    uint64_t adj_before, adj_after, adj_cap;
     // outputs
     uint64_t* out;
     uint64_t capacity;
     uint64_t* bounds_index;  // batch: n_files + 1 entries, else NULL
     uint64_t* d_count;       // receives the total, may be NULL
     // workspace
-    ItemStatus* st;
+    SegState* st;
+    void* groups;            // GroupState per GS segments
     Ctrl* ctrl;
     uint64_t timeout_ns;
     int64_t hold_item;
@@ -64,9 +73,14 @@ uint64_t summary_tiles(int kind, uint64_t nblk);
 cudaError_t launch_summary(const SumLaunch& a, int kind, int grid, cudaStream_t st);
 cudaError_t launch_reset(Ctrl* ctrl, cudaStream_t st);
 
+struct ChainGrids {
+    int spec, groups, output;
+};
 int chain_smem(int rule, uint32_t win);
-int chain_blocks_per_sm(int rule, uint32_t win);
-cudaError_t launch_chain(const ChainLaunch& a, int rule, int grid, cudaStream_t st);
+int spec_blocks_per_sm(int rule, uint32_t win);
+size_t seg_state_bytes();
+size_t group_state_bytes();
+cudaError_t launch_chain(const ChainLaunch& a, int rule, const ChainGrids& g, cudaStream_t st, int* launches);
 
 // batch set-up: item_off (n_files + 1), item_file, ctrl->n_items
 cudaError_t launch_batch_setup(const uint64_t* file_off, uint64_t n_files, uint64_t seg, uint64_t* item_off,

@@ -1,423 +1,655 @@
 // chain.cu -- stage 2: the chunk chain, in parallel and bit-exact.
 //
-// Each chunk starts where the previous one ended, so the chunk starts form a
-// single chain s_{i+1} = next(s_i) (Section 3.3: every algorithm is a loop of
-// extreme byte searches and range scans over one chunk at a time). Chains
-// started at different offsets join only where their cuts coincide, and for
-// RAM and AE on random bytes that can take hundreds of kilobytes, so a single
-// speculative chain per segment would almost never line up with the true
-// one. The stage therefore works per segment ("item") of the input, one warp
-// per item, in four steps:
+// Each chunk starts where the previous one ended (Section 3.3: every
+// algorithm is a loop over one chunk at a time), so the chunk starts form a
+// single chain s_{i+1} = next(s_i). Chains started at different offsets join
+// where their cuts coincide, but on random or text-like bytes that can take
+// hundreds of kilobytes (the gap between two chains moves like a random
+// walk), and inside runs of zeros -- or MAXP stretches without a target --
+// they never join at all. The stage therefore splits the input into
+// segments and describes each segment by a transfer table over many chains:
 //
-//  A. Speculate: each of the 32 lanes runs its own chain (per-thread next())
-//     from a different start spread over the first `span` bytes of the
-//     segment, recording its first KFIRST positions, its count and its exit
-//     (first position at or past the segment end).
-//  B. Stitch: for every distinct exit of the previous segment's 32 chains,
-//     the warp follows the chain from that exit until it lands on a recorded
-//     position of one of this segment's lanes (or reaches the segment end and
-//     matches a lane's exit). The result is a 32-entry table: predecessor
-//     chain -> (this segment's chain, number of boundaries in the segment).
-//  C. Resolve: decoupled look-back. Find the nearest earlier segment whose
-//     true state is published, then carry that state forward through the
-//     tables of the segments in between (warp shuffles), publishing each
-//     segment's true state on the way so that later warps start closer.
-//     Entries the tables do not cover are settled by following the chain
-//     through that segment directly.
-//  D. Output: follow the true chain through the segment once more and write
-//     its boundaries at the global offset found in C.
-//
-// All waits are bounded (globaltimer); on expiry the kernel records
-// ERR_TIMEOUT in the control block and every warp leaves.
+//  k_spec    (one CTA of NW warps per segment)
+//    * Segment bounds: nominal bounds every `seg` bytes are moved forward
+//      out of quiet regions (zero superblocks for RAM/AE, target-less runs
+//      for MAXP), so that every segment starts where chains join quickly.
+//    * Speculate: NL = 32*NW threads each run one chain (per-thread next()
+//      over shared-memory block summaries) from starts spread over the first
+//      `span` bytes; their first KF positions go into a shared-memory hash.
+//    * Stitch: for each distinct exit of the previous segment's NL chains, a
+//      warp follows the chain from that exit until it lands on a hashed
+//      position (or ends on a chain's exit). Result: a table
+//      predecessor chain -> (this segment's chain, boundaries in segment).
+//  k_compose (one warp per group of GS segments): composes the group's tables.
+//  k_scan    (one warp): carries the true state across the group composites
+//            from the start of the data (the first segment of every file is
+//            exact), settling entries no table covers by following the chain.
+//  k_settle  (one warp per group): carries the state through the group's
+//            segments; records each segment's true entry and global offset.
+//  k_output  (one warp per segment): follows the true chain through the
+//            segment and writes its boundaries at that offset.
+// Every wait (a segment on its predecessor's speculation) is bounded.
 #include "cdc_device.cuh"
 #include "cdc_launch.h"
 
 namespace cdc {
 
-struct Lanes {
-    uint32_t fp[KFIRST];  // first positions of this lane's chain (offsets from seg_lo)
-    uint32_t c;           // positions of the chain inside the segment
-    uint64_t x;           // exit of the chain
+// ---- per-segment state --------------------------------------------------------
+
+CDC_HD uint32_t stab_enc(uint32_t slot, uint32_t count) { return (slot << 23) | (count & 0x7FFFFFu); }
+CDC_HD uint32_t stab_slot(uint32_t e) { return (e >> 23) & 0x7Fu; }
+CDC_HD uint32_t stab_count(uint32_t e) { return e & 0x7FFFFFu; }
+constexpr uint32_t STAB_UNKNOWN = 0x80000000u;  // count in low bits, exit in unk_exit
+constexpr uint32_t STAB_CONST = 0x40000000u;    // all entries identical (first segment of a file)
+
+struct __align__(128) SegState {
+    unsigned long long X[NL];         // chain exits (first position >= seg_hi), ~0 if idle
+    unsigned int table[NL];           // predecessor chain -> (chain, count)
+    unsigned long long unk_exit[NL];  // exit of the followed chain for UNKNOWN entries
+    unsigned long long seg_lo, seg_hi, flo, fhi;
+    unsigned int geo;                 // bit0 first of file, bit1 last of file, bit2 empty
+    unsigned int flagA;
+    // written by k_settle
+    unsigned long long entry_pos;     // first true position >= seg_lo (or >= seg_hi)
+    unsigned long long excl;          // boundaries before this segment
+    unsigned int count;               // boundaries inside this segment
+    unsigned int fileidx;
+};
+enum : unsigned int { GEO_FIRST = 1u, GEO_LAST = 2u, GEO_EMPTY = 4u };
+
+size_t seg_state_bytes() { return sizeof(SegState); }
+
+// group composites (k_compose -> k_scan)
+struct __align__(128) GroupState {
+    unsigned int slot[NL];            // state after the group's last segment, or UNRESOLVED
+    unsigned long long count[NL];     // boundaries in the group
+    unsigned int entry_slot;          // written by k_scan: state entering the group
+    unsigned int pad;
+    unsigned long long entry_pos;
+    unsigned long long entry_incl;
+};
+size_t group_state_bytes() { return sizeof(GroupState); }
+constexpr uint32_t NONE = 0xFFFFu;
+constexpr uint32_t UNRESOLVED = 0xFFFEu;  // composite entry not computable without a walk
+
+// ---- segment geometry ------------------------------------------------------------
+
+struct Geo {
+    uint64_t flo, fhi, seg_lo, seg_hi, f;
+    bool first, last, empty;
 };
 
-struct WalkResult {
-    uint32_t code;   // tab_enc(slot, count), or TAB_UNKNOWN when no chain was joined
-    uint64_t exit;   // exit position of the followed chain
-    uint32_t count;  // boundaries inside the segment
-};
-
-// Follow the chain from entry e through [seg_lo, seg_hi) until it joins one
-// of the segment's 32 chains. Warp-uniform: every lane computes the same
-// steps; lane l tests membership in its own chain.
-template <int RULE>
-__device__ WalkResult walk(const SumView& S, const RawView& R, const Prm& P, uint64_t flo, uint64_t fhi,
-                           uint64_t seg_lo, uint64_t seg_hi, bool last, const Lanes& L, uint64_t e) {
-    uint64_t v = e;
-    uint32_t ne = 0;
-    while (v < seg_hi) {
-        int idx = -1;
-#pragma unroll
-        for (int t = KFIRST - 1; t >= 0; t--)
-            if ((uint32_t)t < L.c && seg_lo + L.fp[t] == v) idx = t;
-        uint32_t hm = __ballot_sync(FULL, idx >= 0);
-        if (hm) {
-            int m = __ffs((int)hm) - 1;
-            int im = __shfl_sync(FULL, idx, m);
-            uint32_t cm = __shfl_sync(FULL, L.c, m);
-            uint64_t xm = __shfl_sync(FULL, L.x, m);
-            uint32_t cnt = ne + cm - (uint32_t)im + (last ? 1u : 0u);
-            return {tab_enc((uint32_t)m, cnt), xm, cnt};
-        }
-        v = next_cut<RULE>(S, R, P, flo, fhi, v);
-        ne++;
-    }
-    uint32_t cnt = ne + (last ? 1u : 0u);
-    uint32_t xm = __ballot_sync(FULL, L.x == v);
-    if (xm) return {tab_enc((uint32_t)(__ffs((int)xm) - 1), cnt), v, cnt};
-    return {TAB_UNKNOWN, v, cnt};
-}
-
-// lane 0 waits (bounded) until *f == epoch; false on timeout or error
-__device__ bool wait_flag(const unsigned int* f, uint32_t epoch, const ChainLaunch& A, uint64_t item) {
-    uint32_t ok = 1;
-    if ((threadIdx.x & 31) == 0 && ld_acquire(f) != epoch) {
-        uint64_t t0 = gtimer_ns();
-        for (;;) {
-            if (ld_acquire(f) == epoch) break;
-            if (ld_volatile(&A.ctrl->err)) { ok = 0; break; }
-            if (gtimer_ns() - t0 > A.timeout_ns) {
-                atomicOr(&A.ctrl->err, ERR_TIMEOUT);
-                A.ctrl->err_info = item;
-                ok = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
-    }
-    ok = __shfl_sync(FULL, ok, 0);
-    __syncwarp();
-    return ok != 0;
-}
-
-__device__ __forceinline__ void publish_final(ItemStatus* it, uint32_t slot, uint64_t exit, uint64_t incl,
-                                              uint32_t epoch) {
-    if (ld_acquire(&it->flagFIN) == epoch) return;
-    it->fin_slot = slot;
-    it->fin_exit = exit;
-    it->fin_incl = incl;
-    __threadfence();
-    st_release(&it->flagFIN, epoch);
-}
-
-// True state after segment jt: the chain's slot in jt (or NONE_SLOT), its exit
-// position and the number of boundaries up to and including jt.
-template <int RULE>
-__device__ bool resolve(const ChainLaunch& A, uint32_t epoch, uint64_t jt, const Prm& P, const RawView& R,
-                        uint32_t* o_slot, uint64_t* o_pos, uint64_t* o_incl) {
-    const int lane = threadIdx.x & 31;
-    // 1) nearest segment with a published true state; every later one up to
-    //    jt must have published its table
-    int64_t j = -1;
-    uint64_t t0 = 0;
-    bool timing = false;
+// Move a nominal bound x forward to the first 4 KiB-aligned y whose
+// neighbourhood [y - before, y + after) meets no quiet run (a run of at least
+// `quiet_run` consecutive quiet superblocks, counted over the whole file).
+// The rule depends on y alone, so the result is monotone in x and adjacent
+// segments stay contiguous. Single forward pass.
+__device__ uint64_t adjust_bound(const ChainLaunch& A, uint64_t x, uint64_t flo, uint64_t fhi) {
+    if (A.quiet_run == 0 || x <= flo) return x <= flo ? flo : x;
+    if (x >= fhi) return fhi;
+    const uint64_t cap = x + A.adj_cap;
+    const uint64_t qf = flo >> 12;
+    uint64_t y = x;
+    uint64_t q = (y > flo + A.adj_before ? y - A.adj_before : flo) >> 12;
+    // length of the quiet run that ends just before q
+    uint32_t run = 0;
+    for (uint64_t r = q; r > qf && run < A.quiet_run && A.ssup[r - 1] == 0; r--) run++;
     for (;;) {
-        int64_t base = (int64_t)jt;
-        for (;;) {
-            int64_t i = base - lane;
-            bool valid = i >= 0;
-            uint32_t ff = valid ? ld_acquire(&A.st[i].flagFIN) : 0u;
-            uint32_t fa = valid ? ld_acquire(&A.st[i].flagAGG) : 0u;
-            uint32_t fm = __ballot_sync(FULL, valid && ff == epoch);
-            uint32_t am = __ballot_sync(FULL, !valid || ff == epoch || fa == epoch);
-            if (fm) {
-                int l = __ffs((int)fm) - 1;
-                uint32_t need = l ? ((1u << l) - 1u) : 0u;
-                if ((am & need) == need) j = base - l;
-                break;
-            }
-            if (am != FULL || base < 32) break;
-            base -= 32;
+        const uint64_t qpos = q << 12;
+        if (qpos >= y + A.adj_after || qpos >= fhi) return y;  // clean window found
+        const bool quiet = A.ssup[q] == 0;
+        run = quiet ? run + 1 : 0;
+        if (run >= A.quiet_run) {
+            uint64_t ny = ((q + 1) << 12) + A.adj_before;
+            ny = (ny + 4095) & ~4095ull;
+            if (ny > y) y = ny;
+            if (y >= fhi) return fhi;
+            if (y >= cap) return cap < fhi ? cap : fhi;
         }
-        if (j >= 0) break;
-        uint32_t bad = 0;
-        if (lane == 0) {
-            if (!timing) { t0 = gtimer_ns(); timing = true; }
-            if (ld_volatile(&A.ctrl->err)) bad = 1;
-            else if (gtimer_ns() - t0 > A.timeout_ns) {
-                atomicOr(&A.ctrl->err, ERR_TIMEOUT);
-                A.ctrl->err_info = jt;
-                bad = 1;
-            }
-            __nanosleep(128);
-        }
-        if (__shfl_sync(FULL, bad, 0)) return false;
+        q++;
     }
-    __syncwarp();
-    uint32_t slot = A.st[j].fin_slot;
-    uint64_t pos = A.st[j].fin_exit;
-    uint64_t incl = A.st[j].fin_incl;
-    // 2) carry the state forward, 8 segments per round
-    const SumView Sg{A.smax, A.sarg, nullptr, nullptr, 0, 0};
-    uint64_t i = (uint64_t)j + 1;
-    while (i <= jt) {
-        const uint32_t nbat = (uint32_t)umin64(8, jt - i + 1);
-        uint32_t tb[8];
-#pragma unroll
-        for (int t = 0; t < 8; t++) tb[t] = (uint32_t)t < nbat ? A.st[i + t].table[lane] : 0u;
-        uint32_t done = 0, my_sl = 0, my_cn = 0;
-#pragma unroll
-        for (int t = 0; t < 8; t++) {
-            if ((uint32_t)t < nbat && done == (uint32_t)t) {
-                uint32_t e0 = __shfl_sync(FULL, tb[t], 0);
-                uint32_t e = (e0 & TAB_CONST) ? e0 : (slot < 32 ? __shfl_sync(FULL, tb[t], (int)slot) : TAB_UNKNOWN);
-                if (!(e & TAB_UNKNOWN)) {
-                    slot = tab_slot(e);
-                    if (lane == t) { my_sl = slot; my_cn = tab_count(e); }
-                    done++;
-                }
-            }
-        }
-        if (done) {
-            uint64_t my_pos = 0;
-            if ((uint32_t)lane < done) my_pos = A.st[i + lane].X[my_sl];
-            uint64_t c64 = (uint32_t)lane < done ? my_cn : 0;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                uint64_t o = __shfl_up_sync(FULL, c64, d);
-                if (lane >= d) c64 += o;
-            }
-            uint64_t my_incl = incl + c64;
-            if ((uint32_t)lane < done && (int64_t)(i + lane) != A.hold_item)
-                publish_final(&A.st[i + lane], my_sl, my_pos, my_incl, epoch);
-            pos = __shfl_sync(FULL, my_pos, (int)done - 1);
-            incl = __shfl_sync(FULL, my_incl, (int)done - 1);
-            i += done;
-        }
-        if (done < nbat) {
-            // segment i does not cover this entry: follow the chain through it
-            ItemStatus* it = &A.st[i];
-            Lanes L;
-#pragma unroll
-            for (int t = 0; t < KFIRST; t++) L.fp[t] = it->first[lane][t];
-            L.c = it->cnt[lane];
-            L.x = it->X[lane];
-            const uint64_t s_lo = it->seg_lo, s_hi = it->seg_hi, flo = it->flo, fhi = it->fhi;
-            const bool last = (it->geo & 2u) != 0;
-            WalkResult r = walk<RULE>(Sg, R, P, flo, fhi, s_lo, s_hi, last, L, pos);
-            slot = (r.code & TAB_UNKNOWN) ? NONE_SLOT : tab_slot(r.code);
-            pos = r.exit;
-            incl += r.count;
-            if (lane == 0 && (int64_t)i != A.hold_item) publish_final(it, slot, pos, incl, epoch);
-            i++;
-        }
-    }
-    *o_slot = slot;
-    *o_pos = pos;
-    *o_incl = incl;
-    return true;
 }
 
-template <int RULE>
-__device__ bool process(const ChainLaunch& A, uint64_t item, uint32_t epoch, uint8_t* smem) {
-    const int lane = threadIdx.x & 31;
-    // ---- geometry
-    uint64_t f, flo_l, fhi_l, kin;
+__device__ Geo seg_geo(const ChainLaunch& A, uint64_t item) {
+    Geo g;
+    uint64_t flo_l, fhi_l, kin;
     if (A.file_off == nullptr) {
-        f = 0; flo_l = 0; fhi_l = A.single_len; kin = item;
+        g.f = 0; flo_l = 0; fhi_l = A.single_len; kin = item;
     } else {
-        f = A.item_file[item];
-        flo_l = A.file_off[f];
-        fhi_l = A.file_off[f + 1];
-        kin = item - A.item_off[f];
+        g.f = A.item_file[item];
+        flo_l = A.file_off[g.f];
+        fhi_l = A.file_off[g.f + 1];
+        kin = item - A.item_off[g.f];
     }
-    const uint64_t flo = A.lo + flo_l, fhi = A.lo + fhi_l;
-    const uint64_t seg_lo = flo + kin * A.seg;
-    const uint64_t seg_hi = umin64(seg_lo + A.seg, fhi);
-    const bool first = kin == 0, last = seg_hi == fhi;
-    ItemStatus* me = &A.st[item];
-    const bool hold = (int64_t)item == A.hold_item;
+    g.flo = A.lo + flo_l;
+    g.fhi = A.lo + fhi_l;
+    const uint64_t nlo = g.flo + kin * A.seg, nhi = nlo + A.seg;
+    g.first = kin == 0;
+    g.seg_lo = g.first ? g.flo : adjust_bound(A, nlo, g.flo, g.fhi);
+    g.seg_hi = nhi >= g.fhi ? g.fhi : adjust_bound(A, nhi, g.flo, g.fhi);
+    if (g.seg_hi < g.seg_lo) g.seg_hi = g.seg_lo;
+    g.empty = g.seg_hi == g.seg_lo;
+    g.last = !g.empty && g.seg_hi == g.fhi;
+    return g;
+}
+
+// ---- shared-memory position hash (first KF positions of every chain) ----------
+
+constexpr int HSLOTS = 2048;  // >= 2 * NL * KF (load factor <= 1/2)
+
+__device__ __forceinline__ uint32_t hslot(uint32_t key) { return (key * 2654435761u) >> 21; }  // 11 bits
+
+__device__ __forceinline__ void hinsert(unsigned int* hk, unsigned int* hv, uint32_t key, uint32_t val) {
+    uint32_t s = hslot(key);
+    for (int i = 0; i < HSLOTS; i++) {
+        uint32_t prev = atomicCAS(&hk[s], 0u, key);
+        if (prev == 0u) { hv[s] = val; return; }
+        if (prev == key) return;  // another chain already recorded this position
+        s = (s + 1) & (HSLOTS - 1);
+    }
+}
+
+// value of a position key, or ~0u
+__device__ __forceinline__ uint32_t hfind(const unsigned int* hk, const unsigned int* hv, uint32_t key) {
+    uint32_t s = hslot(key);
+    for (int i = 0; i < HSLOTS; i++) {
+        uint32_t k = hk[s];
+        if (k == key) return hv[s];
+        if (k == 0u) return ~0u;
+        s = (s + 1) & (HSLOTS - 1);
+    }
+    return ~0u;
+}
+
+// ---- bounded waits -------------------------------------------------------------
+
+__device__ bool wait_flag_thread(const unsigned int* f, uint32_t epoch, const ChainLaunch& A, uint64_t item) {
+    if (ld_acquire(f) == epoch) return true;
+    uint64_t t0 = gtimer_ns();
+    for (;;) {
+        if (ld_acquire(f) == epoch) return true;
+        if (ld_volatile(&A.ctrl->err)) return false;
+        if (gtimer_ns() - t0 > A.timeout_ns) {
+            atomicOr(&A.ctrl->err, ERR_TIMEOUT);
+            A.ctrl->err_info = item;
+            return false;
+        }
+        __nanosleep(100);
+    }
+}
+
+// ---- k_spec: speculate and stitch ------------------------------------------------
+
+struct SpecShared {
+    unsigned int hk[HSLOTS];
+    unsigned int hv[HSLOTS];
+    unsigned long long X[NL];
+    unsigned int cnt[NL];
+    unsigned long long geo[5];
+    unsigned long long item;
+    int ok;
+};
+
+template <int RULE>
+__global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
+    extern __shared__ __align__(16) uint8_t dsm[];  // staged summaries: m[win], a[win]
+    __shared__ SpecShared sh;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t epoch = ld_volatile(&A.ctrl->epoch);
+    const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
+                                           : A.n_items;
     const Prm P{A.w, A.mn, A.mx};
     const RawView R{A.base, A.inv};
-
-    // ---- stage this segment's summaries in shared memory
-    SumView S{A.smax, A.sarg, smem, smem + A.win, 0, 0};
-    if (RULE == RULE_RAM || RULE == RULE_AE || RULE == RULE_MAXP) {
-        uint64_t wb0 = (seg_lo >> 6) & ~15ull;
-        uint64_t wn = A.win;
-        if (wb0 + wn > A.nblk_pad) wn = A.nblk_pad > wb0 ? ((A.nblk_pad - wb0) & ~15ull) : 0;
-        for (uint64_t o = (uint64_t)lane * 16; o < wn; o += 512) {
-            *reinterpret_cast<uint4*>(smem + o) = *reinterpret_cast<const uint4*>(A.smax + wb0 + o);
-            if (RULE != RULE_MAXP)
-                *reinterpret_cast<uint4*>(smem + A.win + o) = *reinterpret_cast<const uint4*>(A.sarg + wb0 + o);
+    for (;;) {
+        if (tid == 0) {
+            sh.item = atomicAdd(&A.ctrl->ticket, 1ull);
+            sh.ok = ld_volatile(&A.ctrl->err) == 0;
         }
-        S.wb0 = wb0;
-        S.wn = wn;
-        __syncwarp();
-    }
-
-    // ---- A: 32 speculative chains
-    Lanes L;
-#pragma unroll
-    for (int t = 0; t < KFIRST; t++) L.fp[t] = 0;
-    L.c = 0;
-    L.x = ~0ull;
-    {
-        uint64_t start = ~0ull;
-        if (first) {
-            if (lane == 0) start = flo;
-        } else {
-            uint64_t len = seg_hi - seg_lo;
-            uint64_t d = umin64(A.span, len) / 32;
-            if (d == 0) d = 1;
-            start = seg_lo + (uint64_t)lane * d;
+        for (int i = tid; i < HSLOTS; i += NL) sh.hk[i] = 0;
+        __syncthreads();
+        const uint64_t item = sh.item;
+        if (item >= n_items || !sh.ok) break;
+        if (tid == 0) {
+            Geo g = seg_geo(A, item);
+            sh.geo[0] = g.seg_lo; sh.geo[1] = g.seg_hi; sh.geo[2] = g.flo; sh.geo[3] = g.fhi;
+            sh.geo[4] = (g.first ? GEO_FIRST : 0u) | (g.last ? GEO_LAST : 0u) | (g.empty ? GEO_EMPTY : 0u);
         }
-        if (start < seg_hi) {
-            uint64_t s = start;
-            uint32_t c = 0;
-            while (s < seg_hi) {
-#pragma unroll
-                for (int t = 0; t < KFIRST; t++)
-                    if ((uint32_t)t == c) L.fp[t] = (uint32_t)(s - seg_lo);
-                c++;
-                s = next_cut<RULE>(S, R, P, flo, fhi, s);
+        __syncthreads();
+        const uint64_t seg_lo = sh.geo[0], seg_hi = sh.geo[1], flo = sh.geo[2], fhi = sh.geo[3];
+        const uint32_t geo = (uint32_t)sh.geo[4];
+        const bool first = geo & GEO_FIRST, last = geo & GEO_LAST, empty = geo & GEO_EMPTY;
+        SegState* me = &A.st[item];
+        const bool hold = (int64_t)item == A.hold_item;
+
+        // stage block summaries of [seg_lo, seg_lo + win * 64)
+        SumView S{A.smax, A.sarg, dsm, dsm + A.win, 0, 0};
+        if (RULE == RULE_RAM || RULE == RULE_AE || RULE == RULE_MAXP) {
+            uint64_t wb0 = (seg_lo >> 6) & ~15ull;
+            uint64_t wn = A.win;
+            if (wb0 + wn > A.nblk_pad) wn = A.nblk_pad > wb0 ? ((A.nblk_pad - wb0) & ~15ull) : 0;
+            for (uint64_t o = (uint64_t)tid * 16; o < wn; o += NL * 16) {
+                *reinterpret_cast<uint4*>(dsm + o) = *reinterpret_cast<const uint4*>(A.smax + wb0 + o);
+                if (RULE != RULE_MAXP)
+                    *reinterpret_cast<uint4*>(dsm + A.win + o) = *reinterpret_cast<const uint4*>(A.sarg + wb0 + o);
             }
-            L.c = c;
-            L.x = s;
+            S.wb0 = wb0;
+            S.wn = wn;
         }
-    }
-    me->X[lane] = L.x;
-#pragma unroll
-    for (int t = 0; t < KFIRST; t++) me->first[lane][t] = L.fp[t];
-    me->cnt[lane] = L.c;
-    if (lane == 0) {
-        me->seg_lo = seg_lo;
-        me->seg_hi = seg_hi;
-        me->flo = flo;
-        me->fhi = fhi;
-        me->geo = (first ? 1u : 0u) | (last ? 2u : 0u);
-    }
-    __syncwarp();
-    __threadfence();
-    if (lane == 0 && !hold) st_release(&me->flagA, epoch);
+        __syncthreads();
 
-    // ---- B: stitching table
-    uint32_t tab = TAB_UNKNOWN;
-    if (first) {
-        uint32_t c0 = __shfl_sync(FULL, L.c, 0);
-        tab = tab_enc(0, c0 - 1 + (last ? 1u : 0u)) | TAB_CONST;
-    } else {
-        if (!wait_flag(&A.st[item - 1].flagA, epoch, A, item)) return false;
-        const uint64_t xp = A.st[item - 1].X[lane];
-        uint32_t todo = __ballot_sync(FULL, xp != ~0ull);
-        while (todo) {
-            const int ld = __ffs((int)todo) - 1;
-            const uint64_t e = __shfl_sync(FULL, xp, ld);
-            const uint32_t same = __ballot_sync(FULL, xp == e) & todo;
-            WalkResult r = walk<RULE>(S, R, P, flo, fhi, seg_lo, seg_hi, last, L, e);
-            if ((same >> lane) & 1u) tab = r.code;
-            todo &= ~same;
-        }
-    }
-    me->table[lane] = tab;
-    __syncwarp();
-    __threadfence();
-    if (lane == 0 && !hold) st_release(&me->flagAGG, epoch);
-
-    // ---- C: true entry and global offset
-    uint32_t eslot = NONE_SLOT;
-    uint64_t epos = flo, excl = 0;
-    if (item > 0 && !resolve<RULE>(A, epoch, item - 1, P, R, &eslot, &epos, &excl)) return false;
-    uint32_t mslot;
-    uint64_t mexit;
-    uint32_t mcnt;
-    if (first) {
-        mslot = 0;
-        mexit = __shfl_sync(FULL, L.x, 0);
-        mcnt = tab_count(tab);
-    } else {
-        uint32_t e = eslot < 32 ? __shfl_sync(FULL, tab, (int)eslot) : TAB_UNKNOWN;
-        if (!(e & TAB_UNKNOWN)) {
-            mslot = tab_slot(e);
-            mcnt = tab_count(e);
-            mexit = __shfl_sync(FULL, L.x, (int)mslot);
+        // ---- speculative chains
+        uint64_t x = ~0ull;
+        uint32_t c = 0;
+        if (empty) {
+            // nothing inside: the predecessor's exits pass through unchanged
+            if (!wait_flag_thread(&A.st[item - 1].flagA, epoch, A, item)) sh.ok = 0;
+            else x = A.st[item - 1].X[tid];
         } else {
-            WalkResult r = walk<RULE>(S, R, P, flo, fhi, seg_lo, seg_hi, last, L, epos);
-            mslot = (r.code & TAB_UNKNOWN) ? NONE_SLOT : tab_slot(r.code);
-            mexit = r.exit;
-            mcnt = r.count;
+            uint64_t start = ~0ull;
+            if (first) {
+                if (tid == 0) start = flo;
+            } else {
+                uint64_t d = umin64(A.span, seg_hi - seg_lo) / NL;
+                start = seg_lo + (uint64_t)tid * (d ? d : 1);
+            }
+            if (start < seg_hi) {
+                uint64_t s = start;
+                while (s < seg_hi) {
+                    if (c < KF) hinsert(sh.hk, sh.hv, (uint32_t)(s - seg_lo) + 1u, ((uint32_t)tid << 8) | c);
+                    c++;
+                    s = next_cut<RULE>(S, R, P, flo, fhi, s);
+                }
+                x = s;
+            }
         }
-    }
-    if (lane == 0 && !hold) publish_final(me, mslot, mexit, excl + mcnt, epoch);
+        sh.X[tid] = x;
+        sh.cnt[tid] = c;
+        me->X[tid] = x;
+        if (tid == 0) {
+            me->seg_lo = seg_lo; me->seg_hi = seg_hi; me->flo = flo; me->fhi = fhi; me->geo = geo;
+        }
+        __syncthreads();
+        if (!sh.ok) break;
+        if (tid == 0) {
+            __threadfence();
+            if (!hold) st_release(&me->flagA, epoch);
+        }
 
-    // ---- D: write the boundaries of the true chain
-    {
-        uint64_t v = first ? flo : epos;
-        uint64_t kb = excl;
-        uint64_t held = 0;
-        uint32_t nb = 0;
-        while (v < seg_hi) {
-            if (v != flo) {
-                if ((uint32_t)lane == nb) held = v - flo;
-                if (++nb == 32) {
-                    if (kb + lane < A.capacity) A.out[kb + lane] = held;
-                    kb += 32;
-                    nb = 0;
+        // ---- stitching table: predecessor chain tid -> (chain, count)
+        uint32_t tab;
+        unsigned long long unk = 0;
+        if (first) {
+            tab = stab_enc(0, sh.cnt[0] - 1 + (last ? 1u : 0u)) | STAB_CONST;
+        } else if (empty) {
+            tab = stab_enc((uint32_t)tid, 0);
+        } else {
+            if (tid == 0 && !wait_flag_thread(&A.st[item - 1].flagA, epoch, A, item)) sh.ok = 0;
+            __syncthreads();
+            if (!sh.ok) break;
+            const uint64_t xp = A.st[item - 1].X[tid];
+            tab = STAB_UNKNOWN;
+            uint32_t todo = __ballot_sync(FULL, xp != ~0ull);
+            while (todo) {
+                const int ld = __ffs((int)todo) - 1;
+                const uint64_t e = __shfl_sync(FULL, xp, ld);
+                const uint32_t same = __ballot_sync(FULL, xp == e) & todo;
+                // follow the chain from e (every lane computes the same steps)
+                uint64_t v = e;
+                uint32_t ne = 0, res = STAB_UNKNOWN;
+                while (v < seg_hi) {
+                    uint32_t hv = hfind(sh.hk, sh.hv, (uint32_t)(v - seg_lo) + 1u);
+                    if (hv != ~0u) {
+                        uint32_t m = hv >> 8, idx = hv & 0xFFu;
+                        res = stab_enc(m, ne + sh.cnt[m] - idx + (last ? 1u : 0u));
+                        break;
+                    }
+                    v = next_cut<RULE>(S, R, P, flo, fhi, v);
+                    ne++;
+                }
+                uint64_t ux = 0;
+                if (res == STAB_UNKNOWN) {
+                    // ended at or past seg_hi: does it end on one of the chains' exits?
+                    int m = -1;
+                    for (int j = 0; j < NL && m < 0; j++)
+                        if (sh.X[j] == v) m = j;
+                    res = m >= 0 ? stab_enc((uint32_t)m, ne + (last ? 1u : 0u))
+                                 : (STAB_UNKNOWN | ((ne + (last ? 1u : 0u)) & 0x7FFFFFu));
+                    ux = v;
+                }
+                if ((same >> lane) & 1u) {
+                    tab = res;
+                    unk = ux;
+                }
+                todo &= ~same;
+            }
+        }
+        me->table[tid] = tab;
+        me->unk_exit[tid] = unk;
+        __syncthreads();
+    }
+}
+
+// ---- following the true chain through one segment (global summaries) ----------
+
+// Walk the chain from position v through segment st (warp-uniform). Returns
+// the number of boundaries inside and the exit; *slot receives the chain of
+// the segment that ends on the same exit, or NONE.
+template <int RULE>
+__device__ uint32_t follow(const ChainLaunch& A, const SegState* st, uint64_t v, uint64_t* exit, uint32_t* slot) {
+    const SumView S{A.smax, A.sarg, nullptr, nullptr, 0, 0};
+    const RawView R{A.base, A.inv};
+    const Prm P{A.w, A.mn, A.mx};
+    const uint64_t seg_hi = st->seg_hi, flo = st->flo, fhi = st->fhi;
+    const bool last = st->geo & GEO_LAST;
+    uint32_t n = 0;
+    while (v < seg_hi) {
+        n++;
+        v = next_cut<RULE>(S, R, P, flo, fhi, v);
+    }
+    if (last) n++;
+    *exit = v;
+    const int lane = threadIdx.x & 31;
+    uint32_t found = NONE;
+#pragma unroll
+    for (int j = 0; j < NL / 32; j++) {
+        uint32_t b = __ballot_sync(FULL, st->X[j * 32 + lane] == v);
+        if (b && found == NONE) found = (uint32_t)(j * 32 + __ffs((int)b) - 1);
+    }
+    *slot = found;
+    return n;
+}
+
+// Table entry for a state entering segment st: `slot` is the chain of the
+// previous segment (or NONE: then only the position is known).
+__device__ __forceinline__ uint32_t lookup(uint32_t t0, const uint32_t t[NL / 32], uint32_t slot) {
+    if (__shfl_sync(FULL, t0, 0) & STAB_CONST) return __shfl_sync(FULL, t0, 0);
+    const uint32_t s = slot < NL ? slot : 0;
+    uint32_t v = 0;
+#pragma unroll
+    for (int j = 0; j < NL / 32; j++) {
+        uint32_t x = __shfl_sync(FULL, t[j], (int)(s & 31));
+        if ((s >> 5) == (uint32_t)j) v = x;
+    }
+    return slot < NL ? v : (STAB_UNKNOWN | 0x7FFFFFu);
+}
+
+// One step of the true state through segment i, given its table entry e for
+// the state. (slot, pos): chain of the previous segment, or NONE and the
+// exact position. Returns the boundaries inside segment i.
+template <int RULE>
+__device__ uint32_t step_with(const ChainLaunch& A, uint64_t i, uint32_t e, uint32_t* slot, uint64_t* pos) {
+    const SegState* st = &A.st[i];
+    if (st->geo & GEO_EMPTY) return 0;  // nothing inside: the state passes through
+    if (!(e & STAB_UNKNOWN) || (e & STAB_CONST)) {
+        *slot = stab_slot(e);
+        *pos = 0;
+        return stab_count(e);
+    }
+    if (*slot < NL) {  // the stitch followed this entry to the end without meeting a chain
+        *pos = st->unk_exit[*slot];
+        *slot = NONE;
+        return stab_count(e);
+    }
+    uint64_t ex;
+    uint32_t sl;
+    uint32_t n = follow<RULE>(A, st, *pos, &ex, &sl);
+    *slot = sl;
+    *pos = ex;
+    return n;
+}
+
+// ---- k_compose: group composites ---------------------------------------------------
+
+template <int RULE>
+__global__ void __launch_bounds__(32) k_compose(ChainLaunch A) {
+    if (ld_volatile(&A.ctrl->err)) return;  // a speculation wait ran out: nothing to resolve
+    static_assert(NL == 128, "composition below assumes 4 table entries per lane");
+    const int lane = threadIdx.x;
+    const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
+                                           : A.n_items;
+    const uint64_t ngroups = (n_items + GS - 1) / GS;
+    for (uint64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const uint64_t i0 = g * GS, i1 = umin64(i0 + GS, n_items);
+        uint32_t sl[4];
+        unsigned long long cn[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) { sl[j] = (uint32_t)(lane + 32 * j); cn[j] = 0; }
+        uint32_t nt[4], ngeo;
+#pragma unroll
+        for (int j = 0; j < 4; j++) nt[j] = A.st[i0].table[lane + 32 * j];
+        ngeo = A.st[i0].geo;
+        for (uint64_t i = i0; i < i1; i++) {
+            uint32_t t[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) t[j] = nt[j];
+            const uint32_t geo = ngeo;
+            if (i + 1 < i1) {  // prefetch the next table
+#pragma unroll
+                for (int j = 0; j < 4; j++) nt[j] = A.st[i + 1].table[lane + 32 * j];
+                ngeo = A.st[i + 1].geo;
+            }
+            if (geo & GEO_EMPTY) continue;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t e = lookup(t[0], t, sl[j]);
+                if (sl[j] == UNRESOLVED) continue;
+                if ((e & STAB_UNKNOWN) && !(e & STAB_CONST)) {
+                    sl[j] = UNRESOLVED;
+                } else {
+                    sl[j] = stab_slot(e);
+                    cn[j] += stab_count(e);
                 }
             }
-            v = next_cut<RULE>(S, R, P, flo, fhi, v);
         }
-        if (last) {
-            if ((uint32_t)lane == nb) held = fhi - flo;
-            nb++;
+        GroupState* gs = reinterpret_cast<GroupState*>(A.groups) + g;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            gs->slot[lane + 32 * j] = sl[j];
+            gs->count[lane + 32 * j] = cn[j];
+        }
+    }
+}
+
+// ---- k_scan: the true state entering every group -------------------------------------
+
+template <int RULE>
+__global__ void __launch_bounds__(32) k_scan(ChainLaunch A) {
+    if (ld_volatile(&A.ctrl->err)) return;  // a speculation wait ran out: nothing to resolve
+    const int lane = threadIdx.x;
+    const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
+                                           : A.n_items;
+    const uint64_t ngroups = (n_items + GS - 1) / GS;
+    GroupState* G = reinterpret_cast<GroupState*>(A.groups);
+    uint32_t slot = NONE;
+    uint64_t pos = A.lo, incl = 0;
+    constexpr int B = 4;  // composites prefetched per round
+    for (uint64_t g0 = 0; g0 < ngroups; g0 += B) {
+        uint32_t gsl[B][4], gfirst[B];
+        unsigned long long gcn[B][4];
+#pragma unroll
+        for (int b = 0; b < B; b++) {
+            const uint64_t g = g0 + b;
+            if (g < ngroups) {
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    gsl[b][j] = G[g].slot[lane + 32 * j];
+                    gcn[b][j] = G[g].count[lane + 32 * j];
+                }
+                gfirst[b] = A.st[g * GS].geo & GEO_FIRST;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < B; b++) {
+            const uint64_t g = g0 + b;
+            if (g >= ngroups) break;
+            if (lane == 0) {
+                G[g].entry_slot = slot;
+                G[g].entry_pos = slot < NL ? 0 : pos;
+                G[g].entry_incl = incl;
+            }
+            const uint32_t s = gfirst[b] ? 0u : slot;
+            uint32_t ns = UNRESOLVED;
+            unsigned long long nc = 0;
+            if (s < NL) {
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    uint32_t a = __shfl_sync(FULL, gsl[b][j], (int)(s & 31));
+                    unsigned long long c = __shfl_sync(FULL, gcn[b][j], (int)(s & 31));
+                    if ((s >> 5) == (uint32_t)j) { ns = a; nc = c; }
+                }
+            }
+            if (ns != UNRESOLVED) {
+                slot = ns;
+                incl += nc;
+            } else {
+                // follow the group segment by segment
+                const uint64_t i0 = g * GS, i1 = umin64(i0 + GS, n_items);
+                for (uint64_t i = i0; i < i1; i++) {
+                    uint32_t t[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) t[j] = A.st[i].table[lane + 32 * j];
+                    const uint32_t e = lookup(t[0], t, slot);
+                    incl += step_with<RULE>(A, i, e, &slot, &pos);
+                }
+            }
+        }
+    }
+    if (lane == 0) {
+        A.ctrl->total = incl;
+        if (A.d_count) *A.d_count = incl;
+    }
+}
+
+// ---- k_settle: each segment's true entry and global offset -----------------------------
+
+template <int RULE>
+__global__ void __launch_bounds__(32) k_settle(ChainLaunch A) {
+    if (ld_volatile(&A.ctrl->err)) return;  // a speculation wait ran out: nothing to resolve
+    const int lane = threadIdx.x;
+    const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
+                                           : A.n_items;
+    const uint64_t ngroups = (n_items + GS - 1) / GS;
+    const GroupState* G = reinterpret_cast<const GroupState*>(A.groups);
+    for (uint64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        uint32_t slot = G[g].entry_slot;
+        uint64_t pos = G[g].entry_pos, incl = G[g].entry_incl;
+        const uint64_t i0 = g * GS, i1 = umin64(i0 + GS, n_items);
+        for (uint64_t b0 = i0; b0 < i1; b0 += 32) {
+            // lane t records segment b0 + t: the state before it, its offset and count
+            uint32_t my_slot = NONE, my_cnt = 0;
+            uint64_t my_pos = 0, my_excl = 0;
+            const uint32_t nb = (uint32_t)umin64(32, i1 - b0);
+            uint32_t nt[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) nt[j] = A.st[b0].table[lane + 32 * j];
+            for (uint32_t k = 0; k < nb; k++) {
+                const uint64_t i = b0 + k;
+                uint32_t t[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) t[j] = nt[j];
+                if (k + 1 < nb) {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) nt[j] = A.st[i + 1].table[lane + 32 * j];
+                }
+                if (lane == (int)k) { my_slot = slot; my_pos = pos; my_excl = incl; }
+                const uint32_t e = lookup(t[0], t, slot);
+                const uint32_t n = step_with<RULE>(A, i, e, &slot, &pos);
+                incl += n;
+                if (lane == (int)k) my_cnt = n;
+            }
+            if ((uint32_t)lane < nb) {
+                const uint64_t i = b0 + lane;
+                SegState* st = &A.st[i];
+                const uint32_t geo = st->geo;
+                uint64_t entry = st->flo;
+                if (!(geo & GEO_FIRST)) entry = my_slot < NL ? A.st[i - 1].X[my_slot] : my_pos;
+                st->entry_pos = entry;
+                st->excl = my_excl;
+                st->count = my_cnt;
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// ---- k_output: write the true chain's boundaries -------------------------------------
+
+template <int RULE>
+__global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
+    if (ld_volatile(&A.ctrl->err)) return;  // a speculation wait ran out: nothing to resolve
+    extern __shared__ __align__(16) uint8_t dsm[];
+    const int lane = threadIdx.x;
+    const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
+                                           : A.n_items;
+    const Prm P{A.w, A.mn, A.mx};
+    const RawView R{A.base, A.inv};
+    for (uint64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const SegState* st = &A.st[item];
+        const uint32_t geo = st->geo;
+        const uint64_t seg_lo = st->seg_lo, seg_hi = st->seg_hi, flo = st->flo, fhi = st->fhi;
+        const uint64_t excl = st->excl;
+        const uint32_t cnt = st->count;
+        const bool first = geo & GEO_FIRST, last = geo & GEO_LAST;
+        SumView S{A.smax, A.sarg, dsm, dsm + A.win, 0, 0};
+        if (RULE == RULE_RAM || RULE == RULE_AE || RULE == RULE_MAXP) {
+            uint64_t wb0 = (seg_lo >> 6) & ~15ull;
+            uint64_t wn = A.win;
+            if (wb0 + wn > A.nblk_pad) wn = A.nblk_pad > wb0 ? ((A.nblk_pad - wb0) & ~15ull) : 0;
+            for (uint64_t o = (uint64_t)lane * 16; o < wn; o += 512) {
+                *reinterpret_cast<uint4*>(dsm + o) = *reinterpret_cast<const uint4*>(A.smax + wb0 + o);
+                if (RULE != RULE_MAXP)
+                    *reinterpret_cast<uint4*>(dsm + A.win + o) = *reinterpret_cast<const uint4*>(A.sarg + wb0 + o);
+            }
+            S.wb0 = wb0;
+            S.wn = wn;
+            __syncwarp();
+        }
+        uint64_t v = first ? flo : st->entry_pos;
+        uint64_t kb = excl, held = 0;
+        uint32_t nb = 0;
+        if (!(geo & GEO_EMPTY)) {
+            while (v < seg_hi) {
+                if (v != flo) {
+                    if ((uint32_t)lane == nb) held = v - flo;
+                    if (++nb == 32) {
+                        if (kb + lane < A.capacity) A.out[kb + lane] = held;
+                        kb += 32;
+                        nb = 0;
+                    }
+                }
+                v = next_cut<RULE>(S, R, P, flo, fhi, v);
+            }
+            if (last) {
+                if ((uint32_t)lane == nb) held = fhi - flo;
+                nb++;
+            }
         }
         if ((uint32_t)lane < nb && kb + lane < A.capacity) A.out[kb + lane] = held;
         kb += nb;
-        if (kb - excl != mcnt || (!first && epos < seg_lo)) {
-            if (lane == 0) {
+        if (lane == 0) {
+            if (kb - excl != cnt || (!first && !(geo & GEO_EMPTY) && st->entry_pos < seg_lo)) {
                 atomicOr(&A.ctrl->err, ERR_INTERNAL);
                 A.ctrl->err_info = item;
             }
-        }
-    }
-
-    // ---- per-file offsets and the total
-    if (lane == 0) {
-        if (A.bounds_index && first) {
-            A.bounds_index[f] = excl;
-            for (uint64_t g = f; g > 0 && A.file_off[g - 1] == A.file_off[g]; g--) A.bounds_index[g - 1] = excl;
-        }
-        const uint64_t n_items = A.n_items_dev ? *A.n_items_dev : A.n_items;
-        if (item + 1 == n_items) {
-            const uint64_t total = excl + mcnt;
-            A.ctrl->total = total;
-            if (A.d_count) *A.d_count = total;
-            if (A.bounds_index) {
+            if (A.bounds_index && first) {
+                const uint64_t f = A.item_file[item];
+                A.bounds_index[f] = excl;
+                for (uint64_t g2 = f; g2 > 0 && A.file_off[g2 - 1] == A.file_off[g2]; g2--)
+                    A.bounds_index[g2 - 1] = excl;
+            }
+            if (A.bounds_index && item + 1 == n_items) {
+                const uint64_t f = A.item_file[item];
+                const uint64_t total = excl + cnt;
                 A.bounds_index[A.n_files] = total;
-                for (uint64_t g = A.n_files - 1; g > f && A.file_off[g] == A.file_off[g + 1]; g--)
-                    A.bounds_index[g] = total;
+                for (uint64_t g2 = A.n_files - 1; g2 > f && A.file_off[g2] == A.file_off[g2 + 1]; g2--)
+                    A.bounds_index[g2] = total;
             }
         }
+        __syncwarp();
     }
-    __syncwarp();
-    return true;
 }
 
-template <int RULE>
-__global__ void __launch_bounds__(32) k_chain(ChainLaunch A) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int lane = threadIdx.x & 31;
-    const uint32_t epoch = ld_volatile(&A.ctrl->epoch);
-    const uint64_t n_items =
-        A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev) : A.n_items;
-    for (;;) {
-        unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(&A.ctrl->ticket, 1ull);
-        item = __shfl_sync(FULL, item, 0);
-        if (item >= n_items) break;
-        if (ld_volatile(&A.ctrl->err)) break;
-        if (!process<RULE>(A, item, epoch, smem)) break;
-    }
-}
+// ---- launchers --------------------------------------------------------------------------
 
 int chain_smem(int rule, uint32_t win) {
     if (rule == RULE_RAM || rule == RULE_AE) return 2 * (int)win;
@@ -426,41 +658,48 @@ int chain_smem(int rule, uint32_t win) {
 }
 
 template <int RULE>
-static cudaError_t launch_rule(const ChainLaunch& a, int grid, cudaStream_t st) {
+static cudaError_t launch_rule(const ChainLaunch& a, const ChainGrids& gr, cudaStream_t st, int* launches) {
     int sm = chain_smem(RULE, a.win);
-    cudaError_t e = cudaFuncSetAttribute(k_chain<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaError_t e = cudaFuncSetAttribute(k_spec<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    k_chain<RULE><<<grid, 32, sm, st>>>(a);
+    e = cudaFuncSetAttribute(k_output<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    k_spec<RULE><<<gr.spec, NL, sm, st>>>(a);
+    k_compose<RULE><<<gr.groups, 32, 0, st>>>(a);
+    k_scan<RULE><<<1, 32, 0, st>>>(a);
+    k_settle<RULE><<<gr.groups, 32, 0, st>>>(a);
+    k_output<RULE><<<gr.output, 32, sm, st>>>(a);
+    *launches += 5;
     return cudaGetLastError();
 }
 
-template <int RULE>
-static int occupancy_rule(uint32_t win) {
-    int sm = chain_smem(RULE, win), n = 0;
-    cudaFuncSetAttribute(k_chain<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_chain<RULE>, 32, sm);
-    return n > 0 ? n : 1;
-}
-
-cudaError_t launch_chain(const ChainLaunch& a, int rule, int grid, cudaStream_t st) {
+cudaError_t launch_chain(const ChainLaunch& a, int rule, const ChainGrids& gr, cudaStream_t st, int* launches) {
     switch (rule) {
-    case RULE_RAM: return launch_rule<RULE_RAM>(a, grid, st);
-    case RULE_AE: return launch_rule<RULE_AE>(a, grid, st);
-    case RULE_MAXP: return launch_rule<RULE_MAXP>(a, grid, st);
-    case RULE_RAM_BYTES: return launch_rule<RULE_RAM_BYTES>(a, grid, st);
-    case RULE_AE_BYTES: return launch_rule<RULE_AE_BYTES>(a, grid, st);
-    default: return launch_rule<RULE_MAXP_BYTES>(a, grid, st);
+    case RULE_RAM: return launch_rule<RULE_RAM>(a, gr, st, launches);
+    case RULE_AE: return launch_rule<RULE_AE>(a, gr, st, launches);
+    case RULE_MAXP: return launch_rule<RULE_MAXP>(a, gr, st, launches);
+    case RULE_RAM_BYTES: return launch_rule<RULE_RAM_BYTES>(a, gr, st, launches);
+    case RULE_AE_BYTES: return launch_rule<RULE_AE_BYTES>(a, gr, st, launches);
+    default: return launch_rule<RULE_MAXP_BYTES>(a, gr, st, launches);
     }
 }
 
-int chain_blocks_per_sm(int rule, uint32_t win) {
+template <int RULE>
+static int occ_spec(uint32_t win) {
+    int sm = chain_smem(RULE, win), n = 0;
+    cudaFuncSetAttribute(k_spec<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spec<RULE>, NL, sm);
+    return n > 0 ? n : 1;
+}
+
+int spec_blocks_per_sm(int rule, uint32_t win) {
     switch (rule) {
-    case RULE_RAM: return occupancy_rule<RULE_RAM>(win);
-    case RULE_AE: return occupancy_rule<RULE_AE>(win);
-    case RULE_MAXP: return occupancy_rule<RULE_MAXP>(win);
-    case RULE_RAM_BYTES: return occupancy_rule<RULE_RAM_BYTES>(win);
-    case RULE_AE_BYTES: return occupancy_rule<RULE_AE_BYTES>(win);
-    default: return occupancy_rule<RULE_MAXP_BYTES>(win);
+    case RULE_RAM: return occ_spec<RULE_RAM>(win);
+    case RULE_AE: return occ_spec<RULE_AE>(win);
+    case RULE_MAXP: return occ_spec<RULE_MAXP>(win);
+    case RULE_RAM_BYTES: return occ_spec<RULE_RAM_BYTES>(win);
+    case RULE_AE_BYTES: return occ_spec<RULE_AE_BYTES>(win);
+    default: return occ_spec<RULE_MAXP_BYTES>(win);
     }
 }
 

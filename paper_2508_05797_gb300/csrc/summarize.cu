@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(S1_THREADS) k_summary_max(SumLaunch a) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* buf = smem;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S1_STAGES * S1_TILE);
+    __shared__ unsigned int supmax[S1_STAGES][S1_TILE / 4096];
     const int tid = threadIdx.x;
     if (blockIdx.x == 0 && tid == 0) reset_ctrl(a.ctrl);
     const uint64_t ntiles = (a.nblk * 64 + S1_TILE - 1) / S1_TILE;
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(S1_THREADS) k_summary_max(SumLaunch a) {
         for (int s = 0; s < S1_STAGES; s++) mbar_init(&bar[s], 1);
         fence_mbar_init();
     }
+    if (tid < S1_STAGES * (S1_TILE / 4096)) (&supmax[0][0])[tid] = 0;
     __syncthreads();
     const uint64_t g = gridDim.x;
     if (tid == 0) {
@@ -130,8 +132,16 @@ __global__ void __launch_bounds__(S1_THREADS) k_summary_max(SumLaunch a) {
                     a.sarg[b] = (uint8_t)(63u - (key & 0xFFu));
                 }
             }
+            // each iteration covers one 4 KiB superblock of the tile
+            uint32_t wm = __reduce_max_sync(FULL, key >> 8);
+            if ((tid & 31) == 0 && wm) atomicMax(&supmax[s][it], wm);
         }
         __syncthreads();  // every thread is done with stage s
+        if (tid < S1_TILE / 4096) {
+            uint64_t q = T0 / 4096 + tid;
+            if (q < a.nsup) a.ssup[q] = (uint8_t)supmax[s][tid];
+            supmax[s][tid] = 0;
+        }
         if (tid == 0) {
             uint64_t tn = t + S1_STAGES * g;
             if (tn < ntiles)
@@ -158,6 +168,7 @@ __global__ void __launch_bounds__(MP_THREADS) k_summary_maxp(SumLaunch a) {
     uint8_t* bf = bm + nb;
     uint8_t* bl = bf + nb;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + ((2 * sbytes + 3 * nb + 15) & ~15u));
+    __shared__ unsigned int supcnt[MP_TILE_BLOCKS / 64];
     if (blockIdx.x == 0 && tid == 0) reset_ctrl(a.ctrl);
     const uint64_t ntiles = (a.nblk + MP_TILE_BLOCKS - 1) / MP_TILE_BLOCKS;
     if (tid == 0) {
@@ -165,6 +176,7 @@ __global__ void __launch_bounds__(MP_THREADS) k_summary_maxp(SumLaunch a) {
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
+    if (tid < MP_TILE_BLOCKS / 64) supcnt[tid] = 0;
     __syncthreads();
     const uint64_t g = gridDim.x;
     // stage block 0 stands for global block t * MP_TILE_BLOCKS - hb (negative
@@ -231,14 +243,12 @@ __global__ void __launch_bounds__(MP_THREADS) k_summary_maxp(SumLaunch a) {
         }
         __syncthreads();
         // 2) target test, one thread per tile block
-        for (uint32_t lb = tid; lb < MP_TILE_BLOCKS; lb += MP_THREADS) {
+        for (uint32_t lb = tid; lb < MP_TILE_BLOCKS; lb += MP_THREADS) {  // one block per thread
             const uint64_t gb = t * MP_TILE_BLOCKS + lb;
-            if (gb >= a.nblk) continue;
             const uint32_t sbi = hb + lb;  // stage index of this block
-            uint32_t v = bm[sbi];
-            uint32_t res = 0xFFu;
+            const uint32_t v = bm[sbi];
             const uint64_t p = gb * 64 + bf[sbi];
-            bool ok = v != 0 && bf[sbi] == bl[sbi] && p >= a.lo + w && p + w < a.hi;
+            bool ok = gb < a.nblk && v != 0 && bf[sbi] == bl[sbi] && p >= a.lo + w && p + w < a.hi;
             if (ok) {
                 const uint64_t wl = p - w, wr = p + w;  // window [wl, wr]
                 const uint64_t kb0 = wl >> 6, kb1 = wr >> 6;
@@ -254,8 +264,16 @@ __global__ void __launch_bounds__(MP_THREADS) k_summary_maxp(SumLaunch a) {
                         if (sp[x - blo] >= v) { ok = false; break; }
                 }
             }
-            if (ok) res = bf[sbi];
-            a.smax[gb] = (uint8_t)res;
+            if (gb < a.nblk) a.smax[gb] = ok ? bf[sbi] : (uint8_t)0xFFu;
+            // targets per 4 KiB superblock (64 blocks = 2 warps of this loop)
+            const uint32_t cntw = __popc(__ballot_sync(FULL, ok));
+            if ((tid & 31) == 0 && cntw) atomicAdd(&supcnt[lb >> 6], cntw);
+        }
+        __syncthreads();
+        if (tid < MP_TILE_BLOCKS / 64) {
+            uint64_t q = t * (MP_TILE_BLOCKS / 64) + tid;
+            if (q < a.nsup) a.ssup[q] = (uint8_t)min(supcnt[tid], 255u);
+            supcnt[tid] = 0;
         }
         __syncthreads();
         if (tid == 0) {
