@@ -31,6 +31,7 @@
 // Every wait (a segment on its predecessor's speculation) is bounded.
 #include "cdc_device.cuh"
 #include "cdc_launch.h"
+#include "warp_rules.cuh"
 
 namespace cdc {
 
@@ -133,29 +134,42 @@ __device__ Geo seg_geo(const ChainLaunch& A, uint64_t item) {
     return g;
 }
 
-// ---- shared-memory position hash (first KF positions of every chain) ----------
+// ---- shared-memory position hash -----------------------------------------------
+// Entries are (key << 32) | value with key = position - seg_lo + 1 and value =
+// (chain << 16) | index of the position in that chain. Inserted atomically as
+// one 64-bit word, so a chain that finds its position already present learns
+// at once which chain got there first.
 
-constexpr int HSLOTS = 2048;  // >= 2 * NL * KF (load factor <= 1/2)
+constexpr int HSLOTS = 2048;
+constexpr int HFILL = 1400;  // stop inserting beyond this many entries
 
 __device__ __forceinline__ uint32_t hslot(uint32_t key) { return (key * 2654435761u) >> 21; }  // 11 bits
+constexpr uint32_t H_INSERTED = 0xFFFFFFFFu, H_FULL = 0xFFFFFFFEu;
 
-__device__ __forceinline__ void hinsert(unsigned int* hk, unsigned int* hv, uint32_t key, uint32_t val) {
+// insert; returns H_INSERTED, H_FULL, or the value already stored for key
+__device__ __forceinline__ uint32_t hinsert(unsigned long long* ht, unsigned int* fill, uint32_t key, uint32_t val) {
+    if (*reinterpret_cast<volatile unsigned int*>(fill) >= (unsigned)HFILL) return H_FULL;
+    const unsigned long long ent = ((unsigned long long)key << 32) | val;
     uint32_t s = hslot(key);
-    for (int i = 0; i < HSLOTS; i++) {
-        uint32_t prev = atomicCAS(&hk[s], 0u, key);
-        if (prev == 0u) { hv[s] = val; return; }
-        if (prev == key) return;  // another chain already recorded this position
+    for (int i = 0; i < 64; i++) {
+        unsigned long long prev = atomicCAS(&ht[s], 0ull, ent);
+        if (prev == 0ull) {
+            atomicAdd(fill, 1u);
+            return H_INSERTED;
+        }
+        if ((uint32_t)(prev >> 32) == key) return (uint32_t)prev;
         s = (s + 1) & (HSLOTS - 1);
     }
+    return H_FULL;
 }
 
-// value of a position key, or ~0u
-__device__ __forceinline__ uint32_t hfind(const unsigned int* hk, const unsigned int* hv, uint32_t key) {
+// value stored for key, or ~0u
+__device__ __forceinline__ uint32_t hfind(const unsigned long long* ht, uint32_t key) {
     uint32_t s = hslot(key);
-    for (int i = 0; i < HSLOTS; i++) {
-        uint32_t k = hk[s];
-        if (k == key) return hv[s];
-        if (k == 0u) return ~0u;
+    for (int i = 0; i < 64; i++) {
+        const unsigned long long e = ht[s];
+        if ((uint32_t)(e >> 32) == key) return (uint32_t)e;
+        if (e == 0ull) return ~0u;
         s = (s + 1) & (HSLOTS - 1);
     }
     return ~0u;
@@ -180,11 +194,21 @@ __device__ bool wait_flag_thread(const unsigned int* f, uint32_t epoch, const Ch
 
 // ---- k_spec: speculate and stitch ------------------------------------------------
 
+constexpr int KS = 3;          // per-thread steps per round before the survivors are counted
+constexpr int ALIVE_WARP = 24;  // at most this many chains left: follow them a warp at a time
+
 struct SpecShared {
-    unsigned int hk[HSLOTS];
-    unsigned int hv[HSLOTS];
+    unsigned long long ht[HSLOTS];
+    unsigned int fill;
+    unsigned int nq;
+    unsigned int q_lane[NL];
+    unsigned long long q_s[NL];
+    unsigned int q_c[NL];
     unsigned long long X[NL];
     unsigned int cnt[NL];
+    int mg[NL];            // chain this one merged into, or -1
+    unsigned int mc[NL];   // its own count at the merge position
+    unsigned int mi[NL];   // index of that position in the target chain
     unsigned long long geo[5];
     unsigned long long item;
     int ok;
@@ -205,7 +229,8 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
             sh.item = atomicAdd(&A.ctrl->ticket, 1ull);
             sh.ok = ld_volatile(&A.ctrl->err) == 0;
         }
-        for (int i = tid; i < HSLOTS; i += NL) sh.hk[i] = 0;
+        for (int i = tid; i < HSLOTS; i += NL) sh.ht[i] = 0ull;
+        if (tid == 0) sh.fill = 0;
         __syncthreads();
         const uint64_t item = sh.item;
         if (item >= n_items || !sh.ok) break;
@@ -222,7 +247,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
         const bool hold = (int64_t)item == A.hold_item;
 
         // stage block summaries of [seg_lo, seg_lo + win * 64)
-        SumView S{A.smax, A.sarg, dsm, dsm + A.win, 0, 0};
+        SumView S{A.smax, A.sarg, dsm, dsm + A.win, 0, 0, A.ssup};
         if (RULE == RULE_RAM || RULE == RULE_AE || RULE == RULE_MAXP) {
             uint64_t wb0 = (seg_lo >> 6) & ~15ull;
             uint64_t wn = A.win;
@@ -240,6 +265,8 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
         // ---- speculative chains
         uint64_t x = ~0ull;
         uint32_t c = 0;
+        int mg = -1;
+        uint32_t mi = 0;
         if (empty) {
             // nothing inside: the predecessor's exits pass through unchanged
             if (!wait_flag_thread(&A.st[item - 1].flagA, epoch, A, item)) sh.ok = 0;
@@ -252,16 +279,103 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                 uint64_t d = umin64(A.span, seg_hi - seg_lo) / NL;
                 start = seg_lo + (uint64_t)tid * (d ? d : 1);
             }
-            if (start < seg_hi) {
-                uint64_t s = start;
-                while (s < seg_hi) {
-                    if (c < KF) hinsert(sh.hk, sh.hv, (uint32_t)(s - seg_lo) + 1u, ((uint32_t)tid << 8) | c);
-                    c++;
-                    s = next_cut<RULE>(S, R, P, flo, fhi, s);
+            // rounds of KS per-thread steps while many chains are alive
+            uint64_t s = start;
+            bool alive = start < seg_hi, rec = !first;
+            if (tid == 0) sh.nq = 0;
+            for (;;) {
+                for (int r = 0; r < KS && alive; r++) {
+                    if (rec) {
+                        const uint32_t hr = c < 0xFFFFu ? hinsert(sh.ht, &sh.fill, (uint32_t)(s - seg_lo) + 1u,
+                                                                   ((uint32_t)tid << 16) | c)
+                                                        : H_FULL;
+                        if (hr == H_FULL) {
+                            rec = false;
+                        } else if (hr != H_INSERTED) {  // another chain was here first: same chain from now on
+                            mg = (int)(hr >> 16);
+                            mi = hr & 0xFFFFu;
+                            alive = false;
+                            break;
+                        }
+                    }
+                    uint32_t k;
+                    uint64_t dd;
+                    s = advance<RULE>(S, R, P, flo, fhi, s, seg_hi, &k, &dd);
+                    c += k;
+                    if (s >= seg_hi) alive = false;
                 }
-                x = s;
+                const int n_alive = __syncthreads_count(alive);
+                if (n_alive == 0) break;
+                if (n_alive <= ALIVE_WARP) {
+                    if (alive) {
+                        const unsigned q = atomicAdd(&sh.nq, 1u);
+                        sh.q_lane[q] = (unsigned)tid;
+                        sh.q_s[q] = s;
+                        sh.q_c[q] = c;
+                    }
+                    break;
+                }
+            }
+            x = s;
+        }
+        sh.mg[tid] = mg;
+        sh.mc[tid] = c;
+        sh.mi[tid] = mi;
+        sh.X[tid] = x;
+        sh.cnt[tid] = c;
+        __syncthreads();
+        // the remaining chains, one warp each, every step shared by the 32 lanes
+        if (!empty) {
+            for (unsigned q = (unsigned)(tid >> 5); q < sh.nq; q += NW) {
+                const unsigned l = sh.q_lane[q];
+                uint64_t v = sh.q_s[q];
+                uint32_t cc = sh.q_c[q];
+                bool rec = true;
+                int qmg = -1;
+                uint32_t qmi = 0;
+                while (v < seg_hi) {
+                    if (rec) {
+                        uint32_t hr = H_FULL;
+                        if (lane == 0 && cc < 0xFFFFu)
+                            hr = hinsert(sh.ht, &sh.fill, (uint32_t)(v - seg_lo) + 1u, (l << 16) | cc);
+                        hr = __shfl_sync(FULL, hr, 0);
+                        if (hr == H_FULL) {
+                            rec = false;
+                        } else if (hr != H_INSERTED) {
+                            qmg = (int)(hr >> 16);
+                            qmi = hr & 0xFFFFu;
+                            break;
+                        }
+                    }
+                    uint32_t k;
+                    uint64_t dd;
+                    v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+                    cc += k;
+                }
+                if (lane == 0) {
+                    sh.mg[l] = qmg;
+                    sh.mc[l] = cc;
+                    sh.mi[l] = qmi;
+                    sh.X[l] = v;
+                    sh.cnt[l] = cc;
+                }
             }
         }
+        __syncthreads();
+        mg = sh.mg[tid];
+        x = sh.X[tid];
+        c = sh.cnt[tid];
+        if (mg >= 0) {  // follow the merges to a chain that ran to the end
+            uint32_t acc = 0;
+            int l = tid;
+            while (sh.mg[l] >= 0) {
+                acc += sh.mc[l] - sh.mi[l];
+                l = sh.mg[l];
+            }
+            x = sh.X[l];
+            c = acc + sh.cnt[l];
+        }
+        __syncthreads();
         sh.X[tid] = x;
         sh.cnt[tid] = c;
         me->X[tid] = x;
@@ -297,14 +411,16 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                 uint64_t v = e;
                 uint32_t ne = 0, res = STAB_UNKNOWN;
                 while (v < seg_hi) {
-                    uint32_t hv = hfind(sh.hk, sh.hv, (uint32_t)(v - seg_lo) + 1u);
+                    const uint32_t hv = hfind(sh.ht, (uint32_t)(v - seg_lo) + 1u);
                     if (hv != ~0u) {
-                        uint32_t m = hv >> 8, idx = hv & 0xFFu;
+                        const uint32_t m = hv >> 16, idx = hv & 0xFFFFu;
                         res = stab_enc(m, ne + sh.cnt[m] - idx + (last ? 1u : 0u));
                         break;
                     }
-                    v = next_cut<RULE>(S, R, P, flo, fhi, v);
-                    ne++;
+                    uint32_t k;
+                    uint64_t dd;
+                    v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+                    ne += k;
                 }
                 uint64_t ux = 0;
                 if (res == STAB_UNKNOWN) {
@@ -336,15 +452,17 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
 // the segment that ends on the same exit, or NONE.
 template <int RULE>
 __device__ uint32_t follow(const ChainLaunch& A, const SegState* st, uint64_t v, uint64_t* exit, uint32_t* slot) {
-    const SumView S{A.smax, A.sarg, nullptr, nullptr, 0, 0};
+    const SumView S{A.smax, A.sarg, nullptr, nullptr, 0, 0, A.ssup};
     const RawView R{A.base, A.inv};
     const Prm P{A.w, A.mn, A.mx};
     const uint64_t seg_hi = st->seg_hi, flo = st->flo, fhi = st->fhi;
     const bool last = st->geo & GEO_LAST;
     uint32_t n = 0;
     while (v < seg_hi) {
-        n++;
-        v = next_cut<RULE>(S, R, P, flo, fhi, v);
+        uint32_t k;
+        uint64_t dd;
+        v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+        n += k;
     }
     if (last) n++;
     *exit = v;
@@ -590,7 +708,7 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
         const uint64_t excl = st->excl;
         const uint32_t cnt = st->count;
         const bool first = geo & GEO_FIRST, last = geo & GEO_LAST;
-        SumView S{A.smax, A.sarg, dsm, dsm + A.win, 0, 0};
+        SumView S{A.smax, A.sarg, dsm, dsm + A.win, 0, 0, A.ssup};
         if (RULE == RULE_RAM || RULE == RULE_AE || RULE == RULE_MAXP) {
             uint64_t wb0 = (seg_lo >> 6) & ~15ull;
             uint64_t wn = A.win;
@@ -607,22 +725,27 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
         uint64_t v = first ? flo : st->entry_pos;
         uint64_t kb = excl, held = 0;
         uint32_t nb = 0;
+        // lanes hold up to 32 pending boundaries; flushed as one coalesced store
+        auto emit = [&](uint64_t val) {
+            if ((uint32_t)lane == nb) held = val;
+            if (++nb == 32) {
+                if (kb + lane < A.capacity) A.out[kb + lane] = held;
+                kb += 32;
+                nb = 0;
+            }
+        };
         if (!(geo & GEO_EMPTY)) {
             while (v < seg_hi) {
-                if (v != flo) {
-                    if ((uint32_t)lane == nb) held = v - flo;
-                    if (++nb == 32) {
-                        if (kb + lane < A.capacity) A.out[kb + lane] = held;
-                        kb += 32;
-                        nb = 0;
-                    }
+                uint32_t k;
+                uint64_t dd;
+                const uint64_t e = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+                for (uint32_t i = 0; i < k; i++) {
+                    const uint64_t p = v + i * dd;
+                    if (p != flo) emit(p - flo);
                 }
-                v = next_cut<RULE>(S, R, P, flo, fhi, v);
+                v = e;
             }
-            if (last) {
-                if ((uint32_t)lane == nb) held = fhi - flo;
-                nb++;
-            }
+            if (last) emit(fhi - flo);
         }
         if ((uint32_t)lane < nb && kb + lane < A.capacity) A.out[kb + lane] = held;
         kb += nb;

@@ -129,6 +129,7 @@ struct SumView {
     const uint8_t* sm;
     const uint8_t* sa;
     uint64_t wb0, wn;
+    const uint8_t* sup;  // per 4 KiB superblock: max byte (RAM/AE) or target count (MAXP); may be null
     CDC_HD uint32_t m(uint64_t b) const {
         uint64_t r = b - wb0;
         return (b >= wb0 && r < wn) ? sm[r] : gm[b];
@@ -196,7 +197,7 @@ CDC_HD uint32_t sum_max(const SumView& S, uint64_t b0, uint64_t b1) {
     uint32_t acc = 0;
     for (uint64_t wi = b0 >> 2, we = (b1 + 3) >> 2; wi < we; wi++) {
         acc = vmax4(acc, clip_word(S.m4(wi), wi, b0, b1));
-        if (acc == 0xFFFFFFFFu) break;  // cannot grow further
+        if (vcmpeq4(acc, 0xFFFFFFFFu)) return 255;  // cannot grow further
     }
     return hmax4(acc);
 }
@@ -446,6 +447,111 @@ CDC_HD uint64_t next_cut(const SumView& S, const RawView& R, const Prm& P, uint6
     if (RULE == RULE_RAM_BYTES) return next_ram_bytes(R, P, fhi, s);
     if (RULE == RULE_AE_BYTES) return next_ae_bytes(R, P, fhi, s);
     return next_maxp_bytes(R, P, flo, fhi, s);
+}
+
+// ---- fast-forward over quiet stretches ----------------------------------------
+//
+// Inside a run of zero bytes (complemented 0xFF for AE-Min) RAM and AE cut
+// every w+1 bytes: the window maximum is 0 and the byte after it is >= 0
+// (RAM), no byte exceeds the target 0 (AE). Where MAXP has no target within
+// [s+min-1, s+max) it cuts at s+max. advance() takes such steps in one go;
+// every other step is next_cut().
+
+// first position in [p, bound) whose byte is non-zero, skipping quiet
+// superblocks and zero blocks by their summaries; bound if none
+CDC_HD uint64_t first_nonzero(const SumView& S, const RawView& R, uint64_t p, uint64_t bound) {
+    while (p < bound) {
+        if ((p & 4095) == 0 && S.sup && p + 4096 <= bound && S.sup[p >> 12] == 0) {
+            p += 4096;
+            continue;
+        }
+        const uint64_t b = p >> 6, e = umin64(bound, (b + 1) << 6);
+        if (S.m(b) != 0) {
+            uint32_t val;
+            uint64_t r = raw_first_geq(R, p, e, 1, &val);
+            if (r < e) return r;
+        }
+        p = e;
+    }
+    return bound;
+}
+
+// first MAXP target c with c0 <= c < c1, skipping superblocks without one; c1 if none
+CDC_HD uint64_t first_target(const SumView& S, uint64_t c0, uint64_t c1) {
+    uint64_t p = c0;
+    while (p < c1) {
+        if ((p & 4095) == 0 && S.sup && p + 4096 <= c1 && S.sup[p >> 12] == 0) {
+            p += 4096;
+            continue;
+        }
+        const uint64_t b = p >> 6;
+        const uint32_t o = S.m(b);
+        if (o != 0xFFu) {
+            const uint64_t c = (b << 6) + o;
+            if (c >= p && c < c1) return c;
+        }
+        p = (b + 1) << 6;
+    }
+    return c1;
+}
+
+// One or more chain steps from s (< stop). Returns the next position e and
+// sets *k >= 1, *d: the chain visits s, s+d, ..., s+(k-1)d (all < stop) and
+// then e. Equals k applications of next_cut().
+template <int RULE>
+CDC_HD uint64_t advance(const SumView& S, const RawView& R, const Prm& P, uint64_t flo, uint64_t fhi, uint64_t s,
+                        uint64_t stop, uint32_t* k, uint64_t* d) {
+    if (RULE == RULE_RAM || RULE == RULE_AE) {
+        const uint64_t w = P.w, st = w + 1;
+        // quick test: the window's first and last blocks are all zero
+        if (P.mn <= st && s + w < fhi && S.m(s >> 6) == 0 && S.m((s + w - 1) >> 6) == 0) {
+            // steps i with s_i = s + i*st, s_i + w < z (window and cut byte zero),
+            // s_i + w < fhi (not the tail) and s_i < stop
+            const uint64_t kstop = (stop - 1 - s) / st + 1;
+            const uint64_t kfhi = (fhi - 1 - s - w) / st + 1;
+            uint64_t kmax = kstop < kfhi ? kstop : kfhi;
+            const uint64_t z = first_nonzero(S, R, s, s + (kmax - 1) * st + w + 1);
+            const uint64_t kz = z > s + w ? (z - 1 - s - w) / st + 1 : 0;
+            const uint64_t kk = kz < kmax ? kz : kmax;
+            if (kk >= 2) {
+                *k = (uint32_t)kk;
+                *d = st;
+                return s + kk * st;
+            }
+        }
+    }
+    if (RULE == RULE_MAXP) {
+        const uint64_t e1 = next_maxp(S, P, flo, fhi, s);
+        if (e1 == s + P.mx && e1 < fhi) {
+            // forced cut: later forced cuts until a window reaches the next target
+            const uint64_t mx = P.mx;
+            const uint64_t c0 = umax64(s + P.mn - 1, flo + P.w);
+            const uint64_t cend = fhi > flo + P.w ? fhi - P.w : 0;
+            const uint64_t kstop = (stop - 1 - s) / mx + 1;
+            // forced cut s_i + mx must stay <= fhi: i <= (fhi - s - mx) / mx
+            const uint64_t kfhi = (fhi - s) / mx;
+            uint64_t kmax = kstop < kfhi ? kstop : kfhi;
+            if (kmax >= 2) {
+                const uint64_t lim = umin64(cend, s + kmax * mx);
+                const uint64_t c = c0 < lim ? first_target(S, c0, lim) : lim;
+                // step i is forced while its window [s_i+mn-1, s_i+mx) misses c: s_i + mx <= c
+                const uint64_t kc = c >= s + mx ? (c - s - mx) / mx + 1 : 0;
+                const uint64_t kk = kc < kmax ? kc : kmax;
+                if (kk >= 2) {
+                    *k = (uint32_t)kk;
+                    *d = mx;
+                    return s + kk * mx;
+                }
+            }
+        }
+        *k = 1;
+        *d = e1 - s;
+        return e1;
+    }
+    const uint64_t e = next_cut<RULE>(S, R, P, flo, fhi, s);
+    *k = 1;
+    *d = e - s;
+    return e;
 }
 
 // ---- block summaries (the summary kernel's per-block arithmetic, also used

@@ -32,6 +32,8 @@ def load():
         lib.hc_next.restype = u64
         lib.hc_chain.argtypes = [i32, vp, vp, vp, u32, u32, u32, u32, u64, u64, vp, u64]
         lib.hc_chain.restype = u64
+        lib.hc_chain_adv.argtypes = [i32, vp, vp, vp, vp, u32, u32, u32, u32, u64, u64, u64, vp, u64, vp]
+        lib.hc_chain_adv.restype = u64
         lib.hc_block_max_first.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
         lib.hc_block_max_first.restype = None
         _lib = lib

@@ -145,3 +145,53 @@ def test_block_max_first_matches_numpy():
         m, f = ctypes.c_uint32(), ctypes.c_uint32()
         lib.hc_block_max_first(blk.ctypes.data, ctypes.byref(m), ctypes.byref(f))
         assert m.value == blk.max() and f.value == int(np.argmax(blk))
+
+
+def _superblocks(ar, alg):
+    nsup = (ar.hi + 4095) // 4096 + 2
+    sup = np.zeros(nsup, dtype=np.uint8)
+    nblk = (ar.hi + 63) // 64
+    if alg == "maxp":
+        has = (ar.smax[:nblk] != 0xFF).astype(np.int64)
+        cnt = np.add.reduceat(has, np.arange(0, nblk, 64)) if nblk else np.zeros(0)
+        sup[:cnt.size] = np.minimum(cnt, 255)
+    else:
+        m = ar.smax[:nblk]
+        mx = np.maximum.reduceat(m, np.arange(0, nblk, 64)) if nblk else np.zeros(0)
+        sup[:mx.size] = mx
+    return sup
+
+
+@pytest.mark.parametrize("alg,w,mn,mx", [("ram", 700, 128, 8192), ("ram", 3000, 1024, 30000), ("ae", 700, 128, 8192),
+                                          ("ae_min", 300, 64, 4096), ("maxp", 150, 512, 8192),
+                                          ("maxp", 300, 2048, 65536), ("ram", 64, 65, 2000)])
+def test_fast_forward_matches_oracle(alg, w, mn, mx):
+    """advance(): many steps at once through zero runs (RAM/AE) and through
+    target-less stretches (MAXP), exactly equal to the oracle's chain."""
+    lib = hostcheck.load()
+    orc = oracle.get()
+    rng = np.random.default_rng(w)
+    n = 1_500_000
+    zeros = np.zeros(n, dtype=np.uint8)
+    zeros[rng.integers(0, n, size=40)] = rng.integers(1, 256, size=40)
+    ones = np.full(n, 255, dtype=np.uint8)
+    ones[rng.integers(0, n, size=40)] = rng.integers(0, 255, size=40)
+    mixed = synth.mixed_range(11, 64 << 20, 5 << 20, n)
+    text = synth.mixed_range(1, 4 << 30, 6 << 20, n)  # block 6 of the 4 GiB stream is text-like
+    total_jumps = 0
+    for data in (zeros, ones, mixed, text):
+        for lo in (0, 17):
+            ar = Arena(data, lo, alg, w)
+            sup = _superblocks(ar, alg)
+            base, sm, sa = ar.ptrs()
+            rule = ALG_RULE[alg][0]
+            for (a, b) in ((0, n), (12_345, 12_345 + 400_001)):
+                exp = orc.chunk(alg, np.ascontiguousarray(data[a:b]), w, mn, mx)
+                for stop_every in (0, 65536, 4096):
+                    out = np.zeros(exp.size + 4, dtype=np.uint64)
+                    jumps = np.zeros(1, dtype=np.uint64)
+                    got_n = lib.hc_chain_adv(rule, base, sm, sa, sup.ctypes.data, ar.inv, w, mn, mx, lo + a, lo + b,
+                                             stop_every, out.ctypes.data, out.size, jumps.ctypes.data)
+                    assert got_n == exp.size and np.array_equal(out[:got_n], exp), (alg, lo, a, b, stop_every)
+                    total_jumps += int(jumps[0])
+    assert total_jumps > 0  # the fast path was exercised
