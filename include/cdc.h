@@ -143,7 +143,7 @@ CDC_API cdc_status cdc_sync_status(cdc_handle h, cdc_stream stream);
 /* Tuning and test options (value semantics per option). */
 typedef enum {
     CDC_OPT_SEGMENT = 0,      /* bytes per speculative segment; 0 = automatic */
-    CDC_OPT_SPAN = 1,         /* bytes over which a segment's 32 speculative
+    CDC_OPT_SPAN = 1,         /* bytes over which a segment's 128 speculative
                                  chains start; 0 = automatic */
     CDC_OPT_TIMEOUT_MS = 2,   /* bound on any device-side wait (default 2000) */
     CDC_OPT_FORCE_BYTES = 3,  /* 1 = skip the block summaries and scan raw
@@ -151,9 +151,16 @@ typedef enum {
     CDC_OPT_DEBUG_HOLD_ITEM = 4, /* testing only: the segment with this index
                                  never publishes its state, so its successors
                                  time out (-1 = off, the default) */
-    CDC_OPT_PROFILE = 5       /* 1 = record CUDA events around the stages of
+    CDC_OPT_PROFILE = 5,      /* 1 = record CUDA events around the stages of
                                  every call (up to 1024 calls) for
                                  cdc_profile_collect; setting it clears them */
+    CDC_OPT_STATS = 6,        /* 1 = the chain stage counts its work (chain
+                                 steps, stitch walks, uncovered entries, ...)
+                                 for cdc_stats; costs atomics, testing only */
+    CDC_OPT_WARP_CHAINS = 7   /* speculative chains of a segment are stepped one
+                                 per thread while more than this many are
+                                 alive, then one per warp (all 32 lanes share
+                                 each step); 1..128, 0 = automatic (32) */
 } cdc_option;
 
 CDC_API cdc_status cdc_set_option(cdc_handle h, cdc_option opt, int64_t value);
@@ -170,6 +177,14 @@ CDC_API cdc_status cdc_last_timing(cdc_handle h, float* summary_ms, float* chain
  * and clears them. Any output pointer may be NULL. */
 CDC_API cdc_status cdc_profile_collect(cdc_handle h, int* calls, double* summary_ms, double* chain_ms,
                                        int64_t* launches);
+
+/* Counters of the last call made with CDC_OPT_STATS on (up to n of them,
+ * in this order): segments, single-thread chain steps, whole-warp chain steps
+ * in speculation, merged chains, stitch walks, stitch steps, uncovered table
+ * entries, segments whose position hash filled, fallback walks in the
+ * resolution, output steps, empty segments, chains handed to whole warps.
+ * Synchronises `stream`. */
+CDC_API cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream stream);
 
 /* Number of kernels the last call launched. */
 CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);

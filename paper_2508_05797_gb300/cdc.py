@@ -15,6 +15,11 @@ from . import build as _build
 ALGS = {"ram": 0, "ae": 1, "ae_max": 1, "maxp": 2, "ae_min": 3}
 OPT_SEGMENT, OPT_SPAN, OPT_TIMEOUT_MS, OPT_FORCE_BYTES, OPT_DEBUG_HOLD_ITEM = range(5)
 OPT_PROFILE = 5
+OPT_STATS = 6
+OPT_WARP_CHAINS = 7
+STAT_NAMES = ["segments", "thread_steps", "warp_steps", "merges", "stitch_walks", "stitch_steps", "unknown",
+              "hash_full", "scan_follows", "out_steps", "empty", "survivors", "cyc_setup", "cyc_threads",
+              "cyc_warps", "cyc_stitch"]
 STATUS = ["CDC_OK", "CDC_ERR_INVALID", "CDC_ERR_CAPACITY", "CDC_ERR_CUDA", "CDC_ERR_TIMEOUT",
           "CDC_ERR_NOMEM", "CDC_ERR_INTERNAL"]
 OK, ERR_INVALID, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_INTERNAL = range(7)
@@ -66,6 +71,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "cdc_last_launches": ([vp, ctypes.POINTER(i32)], i32),
             "cdc_profile_collect": ([vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
+            "cdc_stats": ([vp, vp, i32, vp], i32),
             "cdc_status_string": ([i32], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -79,7 +85,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return ["cdc_create", "cdc_destroy", "cdc_chunk", "cdc_chunk_async", "cdc_chunk_batch", "cdc_chunk_host",
             "cdc_reserve", "cdc_sync_status", "cdc_set_option", "cdc_get_option", "cdc_last_timing",
-            "cdc_last_launches", "cdc_profile_collect", "cdc_status_string"]
+            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_status_string"]
 
 
 def alg_id(alg) -> int:
@@ -139,6 +145,12 @@ class Chunker:
         a, b = ctypes.c_float(), ctypes.c_float()
         _check(self.lib.cdc_last_timing(self.h, ctypes.byref(a), ctypes.byref(b)), "cdc_last_timing")
         return a.value, b.value
+
+    def stats(self, stream=None) -> dict:
+        """Work counters of the last call made with OPT_STATS on."""
+        arr = (ctypes.c_uint64 * 16)()
+        _check(self.lib.cdc_stats(self.h, arr, 16, _stream_handle(stream)), "cdc_stats")
+        return {name: int(arr[i]) for i, name in enumerate(STAT_NAMES)}
 
     def last_launches(self) -> int:
         n = ctypes.c_int()

@@ -38,7 +38,7 @@ struct cdc_handle_s {
     size_t host_out_cap = 0;
     Ctrl* pinned_ctrl = nullptr;  // page-locked copy of the control block
     // options
-    int64_t seg = 0, span = 0, timeout_ms = 2000, force_bytes = 0, hold_item = -1;
+    int64_t seg = 0, span = 0, timeout_ms = 2000, force_bytes = 0, hold_item = -1, stats = 0, warp_chains = 0;
     // last-call bookkeeping
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     bool timed = false;
@@ -158,6 +158,13 @@ extern "C" cdc_status cdc_set_option(cdc_handle h, cdc_option opt, int64_t v) {
         return CDC_OK;
     case CDC_OPT_FORCE_BYTES: h->force_bytes = v ? 1 : 0; return CDC_OK;
     case CDC_OPT_DEBUG_HOLD_ITEM: h->hold_item = v; return CDC_OK;
+    case CDC_OPT_STATS:
+        h->stats = v ? 1 : 0;
+        return CDC_OK;
+    case CDC_OPT_WARP_CHAINS:
+        if (v < 0 || v > NL) return CDC_ERR_INVALID;
+        h->warp_chains = v;
+        return CDC_OK;
     case CDC_OPT_PROFILE:
         if (v && !h->prof_ev) {
             cudaSetDevice(h->device);
@@ -183,6 +190,8 @@ extern "C" cdc_status cdc_get_option(cdc_handle h, cdc_option opt, int64_t* v) {
     case CDC_OPT_FORCE_BYTES: *v = h->force_bytes; return CDC_OK;
     case CDC_OPT_DEBUG_HOLD_ITEM: *v = h->hold_item; return CDC_OK;
     case CDC_OPT_PROFILE: *v = h->profile; return CDC_OK;
+    case CDC_OPT_STATS: *v = h->stats; return CDC_OK;
+    case CDC_OPT_WARP_CHAINS: *v = h->warp_chains; return CDC_OK;
     default: return CDC_ERR_INVALID;
     }
 }
@@ -365,6 +374,9 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     c.ctrl = h->ctrl;
     c.timeout_ns = timeout_ns;
     c.hold_item = h->hold_item;
+    c.stats = (int)h->stats;
+    c.warp_chains = h->warp_chains ? (uint32_t)h->warp_chains : 32u;
+    if (h->stats) cudaMemsetAsync(h->ctrl->stats, 0, sizeof(h->ctrl->stats), st);
     if (pl.sum != SUM_NONE) {
         const uint64_t mx4k = ((uint64_t)p.max + 4095) & ~4095ull;
         c.quiet_run = pl.sum == SUM_MAXP ? (uint32_t)(p.max / 8192 > 1 ? p.max / 8192 : 1) : 1u;
@@ -565,5 +577,15 @@ extern "C" cdc_status cdc_profile_collect(cdc_handle h, int* calls, double* summ
     h->prof_launches = 0;
     h->last_ev = nullptr;
     h->timed = false;
+    return CDC_OK;
+}
+
+extern "C" cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream stream) {
+    if (!h || !out || n < 0) return CDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(h->pinned_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return CDC_ERR_CUDA;
+    for (int i = 0; i < n && i < 16; i++) out[i] = h->pinned_ctrl->stats[i];
     return CDC_OK;
 }

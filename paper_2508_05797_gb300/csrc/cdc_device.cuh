@@ -18,7 +18,27 @@ struct Ctrl {
     unsigned long long err_info; // first failing item / position, for diagnostics
     unsigned int epoch;          // launch number; a flag is set when it equals this
     unsigned int err;            // sticky error bits, cleared by the host
-    unsigned int pad[6];
+    unsigned int stats_on;       // 1: kernels accumulate the counters below
+    unsigned int pad[5];
+    unsigned long long stats[16];  // see STAT_* (reset by the host)
+};
+enum : int {
+    STAT_SEGMENTS = 0,      // non-empty segments speculated
+    STAT_THREAD_STEPS = 1,  // chain steps taken by single threads
+    STAT_WARP_STEPS = 2,    // chain steps taken by whole warps (speculation)
+    STAT_MERGES = 3,        // speculative chains stopped on another chain's position
+    STAT_STITCH_WALKS = 4,  // distinct predecessor exits followed
+    STAT_STITCH_STEPS = 5,
+    STAT_UNKNOWN = 6,       // table entries no chain covered
+    STAT_HASH_FULL = 7,     // segments whose position hash filled up
+    STAT_SCAN_FOLLOWS = 8,  // segments followed in the scan / settle fallback
+    STAT_OUT_STEPS = 9,     // steps of the output walks
+    STAT_EMPTY = 10,        // empty segments
+    STAT_SURVIVORS = 11,    // chains handed to whole warps
+    STAT_CYC_SETUP = 12,    // cycles (summed over CTAs): bounds + staging
+    STAT_CYC_THREADS = 13,  //   per-thread speculation rounds
+    STAT_CYC_WARPS = 14,    //   whole-warp survivors + merge resolution
+    STAT_CYC_STITCH = 15    //   waiting for the predecessor + stitching
 };
 enum : unsigned int { ERR_TIMEOUT = 1u, ERR_INTERNAL = 2u };
 

@@ -63,6 +63,8 @@ struct ChainLaunch {
     Ctrl* ctrl;
     uint64_t timeout_ns;
     int64_t hold_item;
+    int stats;               // accumulate Ctrl::stats
+    uint32_t warp_chains;    // per-thread speculation rounds run while more chains than this are alive
 };
 
 int summary_max_smem();

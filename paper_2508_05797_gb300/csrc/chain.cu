@@ -175,6 +175,10 @@ __device__ __forceinline__ uint32_t hfind(const unsigned long long* ht, uint32_t
     return ~0u;
 }
 
+__device__ __forceinline__ void stat_add(const ChainLaunch& A, int k, unsigned long long v) {
+    if (A.stats && v) atomicAdd(&A.ctrl->stats[k], v);
+}
+
 // ---- bounded waits -------------------------------------------------------------
 
 __device__ bool wait_flag_thread(const unsigned int* f, uint32_t epoch, const ChainLaunch& A, uint64_t item) {
@@ -194,16 +198,16 @@ __device__ bool wait_flag_thread(const unsigned int* f, uint32_t epoch, const Ch
 
 // ---- k_spec: speculate and stitch ------------------------------------------------
 
-constexpr int KS = 3;          // per-thread steps per round before the survivors are counted
-constexpr int ALIVE_WARP = 24;  // at most this many chains left: follow them a warp at a time
+constexpr int KS = 3;          // per-thread steps per round before the live chains are compacted
 
 struct SpecShared {
     unsigned long long ht[HSLOTS];
     unsigned int fill;
-    unsigned int nq;
-    unsigned int q_lane[NL];
-    unsigned long long q_s[NL];
-    unsigned int q_c[NL];
+    unsigned int nq;               // live chains (compacted into threads [0, nq))
+    unsigned int nq2;
+    unsigned int q_lane[2][NL];    // chain id, position, count of the live chains
+    unsigned long long q_s[2][NL];
+    unsigned int q_c[2][NL];
     unsigned long long X[NL];
     unsigned int cnt[NL];
     int mg[NL];            // chain this one merged into, or -1
@@ -225,6 +229,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
     const Prm P{A.w, A.mn, A.mx};
     const RawView R{A.base, A.inv};
     for (;;) {
+        long long t_mark = clock64();
         if (tid == 0) {
             sh.item = atomicAdd(&A.ctrl->ticket, 1ull);
             sh.ok = ld_volatile(&A.ctrl->err) == 0;
@@ -262,6 +267,14 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
         }
         __syncthreads();
 
+        auto lap = [&](int k) {
+            if (A.stats && tid == 0) {
+                const long long t = clock64();
+                stat_add(A, k, (unsigned long long)(t - t_mark));
+                t_mark = t;
+            }
+        };
+        lap(STAT_CYC_SETUP);
         // ---- speculative chains
         uint64_t x = ~0ull;
         uint32_t c = 0;
@@ -279,68 +292,99 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                 uint64_t d = umin64(A.span, seg_hi - seg_lo) / NL;
                 start = seg_lo + (uint64_t)tid * (d ? d : 1);
             }
-            // rounds of KS per-thread steps while many chains are alive
-            uint64_t s = start;
-            bool alive = start < seg_hi, rec = !first;
+            // rounds of KS per-thread steps; live chains are compacted into the
+            // lowest threads after every round so that idle warps issue nothing
+            uint32_t tsteps = 0;
             if (tid == 0) sh.nq = 0;
+            __syncthreads();
+            if (start < seg_hi) {
+                const unsigned q = atomicAdd(&sh.nq, 1u);
+                sh.q_lane[0][q] = (unsigned)tid;
+                sh.q_s[0][q] = start;
+                sh.q_c[0][q] = 0;
+            }
+            sh.mg[tid] = -1;
+            sh.X[tid] = ~0ull;
+            sh.cnt[tid] = 0;
+            __syncthreads();
+            int buf = 0;
+            const bool rec = !first;
             for (;;) {
-                for (int r = 0; r < KS && alive; r++) {
-                    if (rec) {
-                        const uint32_t hr = c < 0xFFFFu ? hinsert(sh.ht, &sh.fill, (uint32_t)(s - seg_lo) + 1u,
-                                                                   ((uint32_t)tid << 16) | c)
-                                                        : H_FULL;
-                        if (hr == H_FULL) {
-                            rec = false;
-                        } else if (hr != H_INSERTED) {  // another chain was here first: same chain from now on
-                            mg = (int)(hr >> 16);
-                            mi = hr & 0xFFFFu;
+                const unsigned nq = sh.nq;
+                if (nq <= A.warp_chains) break;  // the rest: one warp per chain
+                if (tid == 0) sh.nq2 = 0;
+                __syncthreads();
+                if ((unsigned)tid < nq) {
+                    const unsigned l = sh.q_lane[buf][tid];
+                    uint64_t s = sh.q_s[buf][tid];
+                    uint32_t c = sh.q_c[buf][tid];
+                    bool alive = true, recl = rec;
+                    for (int r = 0; r < KS; r++) {
+                        if (recl) {
+                            const uint32_t hr = c < 0xFFFFu ? hinsert(sh.ht, &sh.fill, (uint32_t)(s - seg_lo) + 1u,
+                                                                       (l << 16) | c)
+                                                            : H_FULL;
+                            if (hr == H_FULL) {
+                                recl = false;
+                            } else if (hr != H_INSERTED) {  // another chain was here first: same chain from now on
+                                sh.mg[l] = (int)(hr >> 16);
+                                sh.mc[l] = c;
+                                sh.mi[l] = hr & 0xFFFFu;
+                                alive = false;
+                                stat_add(A, STAT_MERGES, 1);
+                                break;
+                            }
+                        }
+                        uint32_t k;
+                        uint64_t dd;
+                        s = advance<RULE>(S, R, P, flo, fhi, s, seg_hi, &k, &dd);
+                        c += k;
+                        tsteps++;
+                        if (s >= seg_hi) {
+                            sh.X[l] = s;
+                            sh.cnt[l] = c;
                             alive = false;
                             break;
                         }
                     }
-                    uint32_t k;
-                    uint64_t dd;
-                    s = advance<RULE>(S, R, P, flo, fhi, s, seg_hi, &k, &dd);
-                    c += k;
-                    if (s >= seg_hi) alive = false;
-                }
-                const int n_alive = __syncthreads_count(alive);
-                if (n_alive == 0) break;
-                if (n_alive <= ALIVE_WARP) {
                     if (alive) {
-                        const unsigned q = atomicAdd(&sh.nq, 1u);
-                        sh.q_lane[q] = (unsigned)tid;
-                        sh.q_s[q] = s;
-                        sh.q_c[q] = c;
+                        const unsigned q = atomicAdd(&sh.nq2, 1u);
+                        sh.q_lane[buf ^ 1][q] = l;
+                        sh.q_s[buf ^ 1][q] = s;
+                        sh.q_c[buf ^ 1][q] = c;
                     }
-                    break;
+                }
+                __syncthreads();
+                if (tid == 0) sh.nq = sh.nq2;
+                buf ^= 1;
+                __syncthreads();
+            }
+            if (A.stats) {
+                unsigned long long tot = tsteps;
+                for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULL, tot, o);
+                if (lane == 0) stat_add(A, STAT_THREAD_STEPS, tot);
+                if (tid == 0) {
+                    stat_add(A, STAT_SEGMENTS, 1);
+                    stat_add(A, STAT_SURVIVORS, sh.nq);
+                    if (sh.fill >= (unsigned)HFILL) stat_add(A, STAT_HASH_FULL, 1);
                 }
             }
-            x = s;
-        }
-        sh.mg[tid] = mg;
-        sh.mc[tid] = c;
-        sh.mi[tid] = mi;
-        sh.X[tid] = x;
-        sh.cnt[tid] = c;
-        __syncthreads();
-        // the remaining chains, one warp each, every step shared by the 32 lanes
-        if (!empty) {
+            // the last few chains, one warp each (every step shared by the 32 lanes)
             for (unsigned q = (unsigned)(tid >> 5); q < sh.nq; q += NW) {
-                const unsigned l = sh.q_lane[q];
-                uint64_t v = sh.q_s[q];
-                uint32_t cc = sh.q_c[q];
-                bool rec = true;
+                const unsigned l = sh.q_lane[buf][q];
+                uint64_t v = sh.q_s[buf][q];
+                uint32_t cc = sh.q_c[buf][q];
+                bool recq = rec;
                 int qmg = -1;
                 uint32_t qmi = 0;
                 while (v < seg_hi) {
-                    if (rec) {
+                    if (recq) {
                         uint32_t hr = H_FULL;
                         if (lane == 0 && cc < 0xFFFFu)
                             hr = hinsert(sh.ht, &sh.fill, (uint32_t)(v - seg_lo) + 1u, (l << 16) | cc);
                         hr = __shfl_sync(FULL, hr, 0);
                         if (hr == H_FULL) {
-                            rec = false;
+                            recq = false;
                         } else if (hr != H_INSERTED) {
                             qmg = (int)(hr >> 16);
                             qmi = hr & 0xFFFFu;
@@ -351,16 +395,27 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                     uint64_t dd;
                     v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
                     cc += k;
+                    if (lane == 0) stat_add(A, STAT_WARP_STEPS, 1);
                 }
                 if (lane == 0) {
                     sh.mg[l] = qmg;
                     sh.mc[l] = cc;
                     sh.mi[l] = qmi;
-                    sh.X[l] = v;
-                    sh.cnt[l] = cc;
+                    if (qmg < 0) {
+                        sh.X[l] = v;
+                        sh.cnt[l] = cc;
+                    }
                 }
             }
         }
+        if (empty) {
+            sh.mg[tid] = -1;
+            sh.X[tid] = x;
+            sh.cnt[tid] = 0;
+            if (tid == 0) stat_add(A, STAT_EMPTY, 1);
+        }
+        __syncthreads();
+        lap(STAT_CYC_THREADS);
         __syncthreads();
         mg = sh.mg[tid];
         x = sh.X[tid];
@@ -388,6 +443,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
             __threadfence();
             if (!hold) st_release(&me->flagA, epoch);
         }
+        lap(STAT_CYC_WARPS);
 
         // ---- stitching table: predecessor chain tid -> (chain, count)
         uint32_t tab;
@@ -421,6 +477,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                     uint64_t dd;
                     v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
                     ne += k;
+                    if (lane == 0) stat_add(A, STAT_STITCH_STEPS, 1);
                 }
                 uint64_t ux = 0;
                 if (res == STAB_UNKNOWN) {
@@ -432,6 +489,10 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                                  : (STAB_UNKNOWN | ((ne + (last ? 1u : 0u)) & 0x7FFFFFu));
                     ux = v;
                 }
+                if (lane == 0) {
+                    stat_add(A, STAT_STITCH_WALKS, 1);
+                    if ((res & STAB_UNKNOWN) && !(res & STAB_CONST)) stat_add(A, STAT_UNKNOWN, 1);
+                }
                 if ((same >> lane) & 1u) {
                     tab = res;
                     unk = ux;
@@ -442,6 +503,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
         me->table[tid] = tab;
         me->unk_exit[tid] = unk;
         __syncthreads();
+        lap(STAT_CYC_STITCH);
     }
 }
 
@@ -511,6 +573,7 @@ __device__ uint32_t step_with(const ChainLaunch& A, uint64_t i, uint32_t e, uint
     uint64_t ex;
     uint32_t sl;
     uint32_t n = follow<RULE>(A, st, *pos, &ex, &sl);
+    if ((threadIdx.x & 31) == 0) stat_add(A, STAT_SCAN_FOLLOWS, 1);
     *slot = sl;
     *pos = ex;
     return n;
@@ -620,12 +683,19 @@ __global__ void __launch_bounds__(32) k_scan(ChainLaunch A) {
                 slot = ns;
                 incl += nc;
             } else {
-                // follow the group segment by segment
+                // follow the group segment by segment (tables prefetched one ahead)
                 const uint64_t i0 = g * GS, i1 = umin64(i0 + GS, n_items);
+                uint32_t nt[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) nt[j] = A.st[i0].table[lane + 32 * j];
                 for (uint64_t i = i0; i < i1; i++) {
                     uint32_t t[4];
 #pragma unroll
-                    for (int j = 0; j < 4; j++) t[j] = A.st[i].table[lane + 32 * j];
+                    for (int j = 0; j < 4; j++) t[j] = nt[j];
+                    if (i + 1 < i1) {
+#pragma unroll
+                        for (int j = 0; j < 4; j++) nt[j] = A.st[i + 1].table[lane + 32 * j];
+                    }
                     const uint32_t e = lookup(t[0], t, slot);
                     incl += step_with<RULE>(A, i, e, &slot, &pos);
                 }
@@ -739,6 +809,7 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
                 uint32_t k;
                 uint64_t dd;
                 const uint64_t e = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+                if (lane == 0) stat_add(A, STAT_OUT_STEPS, 1);
                 for (uint32_t i = 0; i < k; i++) {
                     const uint64_t p = v + i * dd;
                     if (p != flo) emit(p - flo);
