@@ -189,6 +189,44 @@ CDC_API cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream stre
 /* Number of kernels the last call launched. */
 CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
 
+/* ---- chunking without any allocation --------------------------------------
+ *
+ * The paper has no counterpart: it is a property of this library's interface,
+ * not of the chunking method.
+ *
+ * cdc_chunk_static does what cdc_chunk does, on the CURRENT device, without a
+ * handle and without allocating anything: no cudaMalloc / cudaFree, no
+ * allocating library routine, no pinned host memory. Its scratch (block
+ * summaries, per-segment speculation state, control block) is one fixed
+ * array of CDC_STATIC_SCRATCH_BYTES in the library's device image, so it
+ * serves inputs of at most CDC_STATIC_MAX_LEN bytes.
+ *
+ * For callers that cannot allocate: code running under a memory cap that is
+ * already fully claimed (for instance by a caching allocator that owns the
+ * device's free memory), latency-sensitive paths where cudaMalloc / cudaFree
+ * would synchronise the device and stall other streams, and callers that
+ * cannot keep a handle's lifetime (create / destroy) around a call.
+ *
+ * Arguments and results are those of cdc_chunk (`*n`: in = capacity of
+ * out_bounds, out = number of boundaries; CDC_ERR_CAPACITY with `*n` = the
+ * number needed). The call synchronises `stream`.
+ *   - len > CDC_STATIC_MAX_LEN returns CDC_ERR_INVALID and enqueues nothing.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (the CUDA runtime may load the library's device code at that moment)
+ *     and clears the parts that must start at zero: the control block and
+ *     the segments' ready flags. Make that first call before any stream
+ *     capture starts. Every call also clears the control block's error word
+ *     before it launches.
+ *   - The scratch is shared by every caller on a device: calls that overlap
+ *     in time (several host threads, or several streams) race on it and give
+ *     wrong results. Serialise them.
+ */
+#define CDC_STATIC_MAX_LEN ((size_t)16 << 20)
+#define CDC_STATIC_SCRATCH_BYTES ((size_t)2117632)
+
+CDC_API cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
+                                    uint64_t* out_bounds, size_t* n, cdc_stream stream);
+
 CDC_API const char* cdc_status_string(cdc_status s);
 
 #ifdef __cplusplus

@@ -72,6 +72,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "cdc_profile_collect": ([vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
             "cdc_stats": ([vp, vp, i32, vp], i32),
+            "cdc_chunk_static": ([i32, P, vp, sz, vp, ctypes.POINTER(sz), vp], i32),
             "cdc_status_string": ([i32], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -85,7 +86,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return ["cdc_create", "cdc_destroy", "cdc_chunk", "cdc_chunk_async", "cdc_chunk_batch", "cdc_chunk_host",
             "cdc_reserve", "cdc_sync_status", "cdc_set_option", "cdc_get_option", "cdc_last_timing",
-            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_status_string"]
+            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_status_string"]
 
 
 def alg_id(alg) -> int:
@@ -238,6 +239,27 @@ def default_chunker(device: int | None = None) -> Chunker:
 def chunk(data, alg, w: int, mn: int, mx: int, stream=None):
     """Boundaries (int64 CUDA tensor) of a uint8 CUDA tensor on the current stream."""
     return default_chunker(data.device.index).chunk(data, alg, w, mn, mx, stream=stream)
+
+
+STATIC_MAX_LEN = 16 << 20
+
+
+def chunk_static(data, alg, w: int, mn: int, mx: int, out=None, stream=None):
+    """cdc_chunk_static: boundaries of a uint8 CUDA tensor (at most
+    STATIC_MAX_LEN bytes) on the current device, with the library's fixed
+    scratch and no handle. The library allocates nothing; `out` (int64 CUDA
+    tensor) is allocated here when not given. Calls must not overlap."""
+    import torch
+    assert data.dtype == torch.uint8 and data.is_cuda and data.is_contiguous()
+    lib = load_library()
+    n = data.numel()
+    if out is None:
+        out = torch.empty(max_boundaries(n, mn), dtype=torch.int64, device=data.device)
+    cap = ctypes.c_size_t(out.numel())
+    st = lib.cdc_chunk_static(alg_id(alg), Params(w, mn, mx), data.data_ptr() if n else None, n, out.data_ptr(),
+                              ctypes.byref(cap), _stream_handle(stream))
+    _check(st, "cdc_chunk_static (count %d)" % cap.value)
+    return out[:cap.value]
 
 
 def chunk_batch(arena, file_off, alg, w: int, mn: int, mx: int, stream=None):

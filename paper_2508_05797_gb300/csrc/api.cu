@@ -5,6 +5,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "../../include/cdc.h"
 #include "cdc_device.cuh"
 #include "cdc_launch.h"
@@ -588,4 +590,174 @@ extern "C" cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream s
         return CDC_ERR_CUDA;
     for (int i = 0; i < n && i < 16; i++) out[i] = h->pinned_ctrl->stats[i];
     return CDC_OK;
+}
+
+// ---- cdc_chunk_static: the chunk path on one fixed scratch array ----------------
+//
+// Same plan, kernels and launch order as run() for a single stream, but every
+// workspace pointer points into g_fixed_scratch, so nothing is allocated.
+// Layout (byte offsets, each part 256-byte aligned):
+//   control block | smax | sarg | ssup | segment states | group states
+
+namespace {
+constexpr uint64_t round256(uint64_t x) { return (x + 255) & ~255ull; }
+constexpr uint64_t kFixMaxLen = CDC_STATIC_MAX_LEN;
+constexpr uint64_t kFixMinSeg = 32u << 10;  // pick_seg() never picks less
+// data may start up to 63 bytes into its 64-byte block
+constexpr uint64_t kFixBlocks = ((kFixMaxLen + 63 + 63) / 64 + 15) & ~15ull;
+constexpr uint64_t kFixSumBytes = round256(kFixBlocks + 64);
+constexpr uint64_t kFixSupBytes = round256((kFixMaxLen + 63 + 4095) / 4096 + 64);
+constexpr uint64_t kFixItems = kFixMaxLen / kFixMinSeg + 1;
+constexpr uint64_t kFixSegSlot = 3072;    // >= sizeof(SegState), checked at set-up
+constexpr uint64_t kFixGroupSlot = 2048;  // >= sizeof(GroupState), checked at set-up
+constexpr uint64_t kFixGroups = kFixItems / GS + 2;
+constexpr uint64_t kFixCtrlBytes = 256;
+constexpr uint64_t kFixOffSmax = kFixCtrlBytes;
+constexpr uint64_t kFixOffSarg = kFixOffSmax + kFixSumBytes;
+constexpr uint64_t kFixOffSup = kFixOffSarg + kFixSumBytes;
+constexpr uint64_t kFixOffSt = kFixOffSup + kFixSupBytes;
+constexpr uint64_t kFixOffGroups = kFixOffSt + kFixItems * kFixSegSlot;
+constexpr uint64_t kFixTotal = kFixOffGroups + kFixGroups * kFixGroupSlot;
+static_assert(kFixTotal == CDC_STATIC_SCRATCH_BYTES, "scratch layout and header disagree");
+static_assert(sizeof(Ctrl) <= kFixCtrlBytes, "control block does not fit");
+constexpr int kFixMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_fixed_scratch[kFixTotal];
+
+static std::mutex g_fixed_mu;
+static uint8_t* g_fixed_ptr[kFixMaxDevices];  // device address of the scratch, per device
+
+// Device address of the scratch on `dev` (the current device). The first call
+// per device looks it up and zeroes the control block (its epoch counter) and
+// the segment states (their ready flags); later calls only read the cache.
+static cdc_status fixed_scratch(int dev, cudaStream_t st, uint8_t** out) {
+    if (dev < 0 || dev >= kFixMaxDevices) return CDC_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_fixed_mu);
+    if (!g_fixed_ptr[dev]) {
+        if (seg_state_bytes() > kFixSegSlot || group_state_bytes() > kFixGroupSlot) return CDC_ERR_INTERNAL;
+        uint8_t* p = nullptr;
+        if (cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_fixed_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return CDC_ERR_CUDA;
+        }
+        if (cudaMemsetAsync(p, 0, kFixCtrlBytes, st) != cudaSuccess ||
+            cudaMemsetAsync(p + kFixOffSt, 0, kFixItems * kFixSegSlot, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return CDC_ERR_CUDA;
+        g_fixed_ptr[dev] = p;
+    }
+    *out = g_fixed_ptr[dev];
+    return CDC_OK;
+}
+
+extern "C" cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
+                                       uint64_t* out_bounds, size_t* n, cdc_stream stream) {
+    if (!n || !valid_params(alg, p)) return CDC_ERR_INVALID;
+    if (len == 0) {
+        *n = 0;
+        return CDC_OK;
+    }
+    if (!data || !out_bounds || len > kFixMaxLen) return CDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CDC_ERR_CUDA;
+    uint8_t* scr = nullptr;
+    cdc_status s = fixed_scratch(dev, st, &scr);
+    if (s != CDC_OK) return s;
+    Ctrl* ctrl = reinterpret_cast<Ctrl*>(scr);
+
+    // the plan and geometry a default handle would pick (fields are only read)
+    cdc_handle_s cfg;
+    cfg.device = dev;
+    cudaDeviceGetAttribute(&cfg.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    const Plan pl = make_plan(&cfg, alg, p);
+    const Geo g = geometry(data, len);
+    const uint64_t seg = pick_seg(&cfg, len, 1);
+    const uint64_t items = (len + seg - 1) / seg;
+    if (items > kFixItems || g.nblk_pad + 64 > kFixSumBytes || g.nsup + 64 > kFixSupBytes) return CDC_ERR_INTERNAL;
+    const uint64_t timeout_ns = (uint64_t)cfg.timeout_ms * 1000000ull;
+
+    if (cudaMemsetAsync(&ctrl->err, 0, sizeof(unsigned int), st) != cudaSuccess) return CDC_ERR_CUDA;
+    int launches = 0;
+    if (pl.sum != SUM_NONE) {
+        SumLaunch a;
+        a.base = g.base;
+        a.lo = g.lo; a.hi = g.hi; a.glo = g.glo; a.ghi = g.ghi;
+        a.nblk = g.nblk;
+        a.smax = scr + kFixOffSmax;
+        a.sarg = pl.sum != SUM_MAXP ? scr + kFixOffSarg : nullptr;
+        a.ssup = scr + kFixOffSup;
+        a.nsup = g.nsup;
+        a.w = p.w;
+        a.halo_blocks = pl.halo;
+        a.timeout_ns = timeout_ns;
+        a.ctrl = ctrl;
+        uint64_t tiles = summary_tiles(pl.sum, g.nblk);
+        uint64_t grid = (uint64_t)cfg.sm_count * summary_blocks_per_sm(pl.sum, pl.halo);
+        if (grid > tiles) grid = tiles;
+        if (grid < 1) grid = 1;
+        if (launch_summary(a, pl.sum, (int)grid, st) != cudaSuccess) return CDC_ERR_CUDA;
+    } else {
+        if (launch_reset(ctrl, st) != cudaSuccess) return CDC_ERR_CUDA;
+    }
+    ChainLaunch c;
+    memset(&c, 0, sizeof c);
+    c.base = g.base;
+    c.lo = g.lo;
+    c.hi = g.hi;
+    c.smax = scr + kFixOffSmax;
+    c.sarg = pl.sum != SUM_MAXP ? scr + kFixOffSarg : scr + kFixOffSmax;
+    c.ssup = scr + kFixOffSup;
+    c.nblk_pad = g.nblk_pad;
+    c.w = p.w; c.mn = p.min; c.mx = p.max;
+    c.inv = pl.inv;
+    c.file_off = nullptr;
+    c.single_len = len;
+    c.n_files = 1;
+    c.n_items = items;
+    c.seg = seg;
+    c.span = pick_span(&cfg, p, seg);
+    c.win = pick_win(p, seg);
+    c.out = out_bounds;
+    c.capacity = *n;
+    c.st = reinterpret_cast<SegState*>(scr + kFixOffSt);
+    c.groups = scr + kFixOffGroups;
+    c.ctrl = ctrl;
+    c.timeout_ns = timeout_ns;
+    c.hold_item = -1;
+    c.warp_chains = 32u;
+    if (pl.sum != SUM_NONE) {
+        const uint64_t mx4k = ((uint64_t)p.max + 4095) & ~4095ull;
+        c.quiet_run = pl.sum == SUM_MAXP ? (uint32_t)(p.max / 8192 > 1 ? p.max / 8192 : 1) : 1u;
+        c.adj_before = ((mx4k / 4) + 4095) & ~4095ull;
+        c.adj_after = mx4k;
+        c.adj_cap = 64ull << 20;
+    }
+    ChainGrids gr;
+    const uint64_t ngroups = (items + GS - 1) / GS;
+    const uint64_t gs = (uint64_t)cfg.sm_count * spec_blocks_per_sm(pl.rule, c.win);
+    gr.spec = (int)(gs < items ? gs : items);
+    gr.groups = (int)(ngroups < (uint64_t)cfg.sm_count * 16 ? ngroups : (uint64_t)cfg.sm_count * 16);
+    gr.output = (int)(items < (uint64_t)cfg.sm_count * 32 ? items : (uint64_t)cfg.sm_count * 32);
+    if (gr.spec < 1) gr.spec = 1;
+    if (gr.groups < 1) gr.groups = 1;
+    if (gr.output < 1) gr.output = 1;
+    if (launch_chain(c, pl.rule, gr, st, &launches) != cudaSuccess) return CDC_ERR_CUDA;
+
+    // count and error word back to pageable host memory (no staging buffer of ours)
+    uint64_t total = 0;
+    unsigned int err = 0;
+    if (cudaMemcpyAsync(&total, &ctrl->total, sizeof total, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&err, &ctrl->err, sizeof err, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return CDC_ERR_CUDA;
+    if (err) {
+        cudaMemsetAsync(&ctrl->err, 0, sizeof(unsigned int), st);
+        cudaStreamSynchronize(st);
+        return (err & ERR_TIMEOUT) ? CDC_ERR_TIMEOUT : CDC_ERR_INTERNAL;
+    }
+    const size_t cap = *n;
+    *n = (size_t)total;
+    return total > cap ? CDC_ERR_CAPACITY : CDC_OK;
 }
