@@ -43,13 +43,22 @@ CDC_HD uint32_t stab_count(uint32_t e) { return e & 0x7FFFFFu; }
 constexpr uint32_t STAB_UNKNOWN = 0x80000000u;  // count in low bits, exit in unk_exit
 constexpr uint32_t STAB_CONST = 0x40000000u;    // all entries identical (first segment of a file)
 
+constexpr int NU = 8;  // uncovered positions resolved per segment
+
 struct __align__(128) SegState {
     unsigned long long X[NL];         // chain exits (first position >= seg_hi), ~0 if idle
     unsigned int table[NL];           // predecessor chain -> (chain, count)
     unsigned long long unk_exit[NL];  // exit of the followed chain for UNKNOWN entries
     unsigned long long seg_lo, seg_hi, flo, fhi;
     unsigned int geo;                 // bit0 first of file, bit1 last of file, bit2 empty
-    unsigned int flagA;
+    unsigned int flagA;               // X and geometry published
+    unsigned int flagB;               // table and unk_exit published
+    unsigned int ures_n;              // entries of ures_* below
+    // positions that reach this segment off every chain (the nearest non-empty
+    // predecessor's uncovered exits), each followed here like a stitch walk
+    unsigned long long ures_pos[NU];
+    unsigned long long ures_exit[NU]; // exit when that walk met no chain either
+    unsigned int ures_val[NU];        // table encoding of the walk's result
     // written by k_settle
     unsigned long long entry_pos;     // first true position >= seg_lo (or >= seg_hi)
     unsigned long long excl;          // boundaries before this segment
@@ -215,6 +224,7 @@ struct SpecShared {
     unsigned int mi[NL];   // index of that position in the target chain
     unsigned long long geo[5];
     unsigned long long item;
+    unsigned long long qitem;  // nearest non-empty predecessor
     int ok;
 };
 
@@ -445,6 +455,43 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
         }
         lap(STAT_CYC_WARPS);
 
+        // Follow the chain from e (every lane of the warp computes the same
+        // steps) until it lands on a hashed position of a chain of this
+        // segment, or reaches seg_hi. Returns the table encoding; *ux receives
+        // the exit when no chain was met (0 otherwise).
+        auto stitch_walk = [&](uint64_t e, uint64_t* ux) -> uint32_t {
+            uint64_t v = e;
+            uint32_t ne = 0, res = STAB_UNKNOWN;
+            while (v < seg_hi) {
+                const uint32_t hv = hfind(sh.ht, (uint32_t)(v - seg_lo) + 1u);
+                if (hv != ~0u) {
+                    const uint32_t m = hv >> 16, idx = hv & 0xFFFFu;
+                    res = stab_enc(m, ne + sh.cnt[m] - idx + (last ? 1u : 0u));
+                    break;
+                }
+                uint32_t k;
+                uint64_t dd;
+                v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+                ne += k;
+                if (lane == 0) stat_add(A, STAT_STITCH_STEPS, 1);
+            }
+            *ux = 0;
+            if (res == STAB_UNKNOWN) {
+                // ended at or past seg_hi: does it end on one of the chains' exits?
+                int m = -1;
+                for (int j = 0; j < NL && m < 0; j++)
+                    if (sh.X[j] == v) m = j;
+                res = m >= 0 ? stab_enc((uint32_t)m, ne + (last ? 1u : 0u))
+                             : (STAB_UNKNOWN | ((ne + (last ? 1u : 0u)) & 0x7FFFFFu));
+                *ux = v;
+            }
+            if (lane == 0) {
+                stat_add(A, STAT_STITCH_WALKS, 1);
+                if (res & STAB_UNKNOWN) stat_add(A, STAT_UNKNOWN, 1);
+            }
+            return res;
+        };
+
         // ---- stitching table: predecessor chain tid -> (chain, count)
         uint32_t tab;
         unsigned long long unk = 0;
@@ -463,36 +510,8 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                 const int ld = __ffs((int)todo) - 1;
                 const uint64_t e = __shfl_sync(FULL, xp, ld);
                 const uint32_t same = __ballot_sync(FULL, xp == e) & todo;
-                // follow the chain from e (every lane computes the same steps)
-                uint64_t v = e;
-                uint32_t ne = 0, res = STAB_UNKNOWN;
-                while (v < seg_hi) {
-                    const uint32_t hv = hfind(sh.ht, (uint32_t)(v - seg_lo) + 1u);
-                    if (hv != ~0u) {
-                        const uint32_t m = hv >> 16, idx = hv & 0xFFFFu;
-                        res = stab_enc(m, ne + sh.cnt[m] - idx + (last ? 1u : 0u));
-                        break;
-                    }
-                    uint32_t k;
-                    uint64_t dd;
-                    v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
-                    ne += k;
-                    if (lane == 0) stat_add(A, STAT_STITCH_STEPS, 1);
-                }
-                uint64_t ux = 0;
-                if (res == STAB_UNKNOWN) {
-                    // ended at or past seg_hi: does it end on one of the chains' exits?
-                    int m = -1;
-                    for (int j = 0; j < NL && m < 0; j++)
-                        if (sh.X[j] == v) m = j;
-                    res = m >= 0 ? stab_enc((uint32_t)m, ne + (last ? 1u : 0u))
-                                 : (STAB_UNKNOWN | ((ne + (last ? 1u : 0u)) & 0x7FFFFFu));
-                    ux = v;
-                }
-                if (lane == 0) {
-                    stat_add(A, STAT_STITCH_WALKS, 1);
-                    if ((res & STAB_UNKNOWN) && !(res & STAB_CONST)) stat_add(A, STAT_UNKNOWN, 1);
-                }
+                uint64_t ux;
+                const uint32_t res = stitch_walk(e, &ux);
                 if ((same >> lane) & 1u) {
                     tab = res;
                     unk = ux;
@@ -502,6 +521,58 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
         }
         me->table[tid] = tab;
         me->unk_exit[tid] = unk;
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            if (!hold) st_release(&me->flagB, epoch);
+        }
+
+        // ---- uncovered exits of the nearest non-empty predecessor (empty
+        // segments pass positions through unchanged): follow each distinct one
+        // here, so that the resolution kernels need not walk this segment
+        if (tid == 0) {
+            uint64_t q = item - 1;  // flagA of item - 1 implies flagA of the empty run before it
+            if (!first && !empty) {
+                while (q > 0 && (A.st[q].geo & GEO_EMPTY) && !(A.st[q].geo & GEO_FIRST)) q--;
+                if (!wait_flag_thread(&A.st[q].flagB, epoch, A, item)) sh.ok = 0;
+            }
+            sh.qitem = q;
+        }
+        __syncthreads();
+        if (!sh.ok) break;
+        if (!first && !empty && tid < 32) {
+            const SegState* qs = &A.st[sh.qitem];
+            uint64_t up[NL / 32];
+#pragma unroll
+            for (int j = 0; j < NL / 32; j++) {
+                const uint32_t t = qs->table[lane + 32 * j];
+                up[j] = ((t & STAB_UNKNOWN) && !(t & STAB_CONST)) ? qs->unk_exit[lane + 32 * j] : ~0ull;
+            }
+            uint32_t nu = 0;
+            for (int j = 0; j < NL / 32; j++) {
+                uint32_t todo = __ballot_sync(FULL, up[j] != ~0ull);
+                while (todo && nu < (uint32_t)NU) {
+                    const int ld = __ffs((int)todo) - 1;
+                    const uint64_t e = __shfl_sync(FULL, up[j], ld);
+                    // drop e everywhere (it may repeat in later words too)
+#pragma unroll
+                    for (int jj = 0; jj < NL / 32; jj++)
+                        if (up[jj] == e) up[jj] = ~0ull;
+                    todo = __ballot_sync(FULL, up[j] != ~0ull);
+                    uint64_t ux;
+                    const uint32_t res = stitch_walk(e, &ux);
+                    if (lane == 0) {
+                        me->ures_pos[nu] = e;
+                        me->ures_exit[nu] = ux;
+                        me->ures_val[nu] = res;
+                    }
+                    nu++;
+                }
+            }
+            if (lane == 0) me->ures_n = nu;
+        } else if (tid == 0) {
+            me->ures_n = 0;
+        }
         __syncthreads();
         lap(STAT_CYC_STITCH);
     }
@@ -570,10 +641,26 @@ __device__ uint32_t step_with(const ChainLaunch& A, uint64_t i, uint32_t e, uint
         *slot = NONE;
         return stab_count(e);
     }
+    // off every chain at *pos: the segment may have followed that position already
+    const int lane = threadIdx.x & 31;
+    const uint32_t nu = st->ures_n;
+    const uint32_t hit = __ballot_sync(FULL, (uint32_t)lane < nu && lane < NU && st->ures_pos[lane < NU ? lane : 0] == *pos);
+    if (hit) {
+        const int l = __ffs((int)hit) - 1;
+        const uint32_t v = st->ures_val[l];
+        if (!(v & STAB_UNKNOWN)) {
+            *slot = stab_slot(v);
+            *pos = 0;
+        } else {
+            *slot = NONE;
+            *pos = st->ures_exit[l];
+        }
+        return stab_count(v);
+    }
     uint64_t ex;
     uint32_t sl;
     uint32_t n = follow<RULE>(A, st, *pos, &ex, &sl);
-    if ((threadIdx.x & 31) == 0) stat_add(A, STAT_SCAN_FOLLOWS, 1);
+    if (lane == 0) stat_add(A, STAT_SCAN_FOLLOWS, 1);
     *slot = sl;
     *pos = ex;
     return n;
@@ -592,9 +679,9 @@ __global__ void __launch_bounds__(32) k_compose(ChainLaunch A) {
     for (uint64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const uint64_t i0 = g * GS, i1 = umin64(i0 + GS, n_items);
         uint32_t sl[4];
-        unsigned long long cn[4];
+        unsigned long long cn[4], ps[4];  // ps: position while sl == NONE (off every chain)
 #pragma unroll
-        for (int j = 0; j < 4; j++) { sl[j] = (uint32_t)(lane + 32 * j); cn[j] = 0; }
+        for (int j = 0; j < 4; j++) { sl[j] = (uint32_t)(lane + 32 * j); cn[j] = 0; ps[j] = 0; }
         uint32_t nt[4], ngeo;
 #pragma unroll
         for (int j = 0; j < 4; j++) nt[j] = A.st[i0].table[lane + 32 * j];
@@ -614,18 +701,34 @@ __global__ void __launch_bounds__(32) k_compose(ChainLaunch A) {
             for (int j = 0; j < 4; j++) {
                 const uint32_t e = lookup(t[0], t, sl[j]);
                 if (sl[j] == UNRESOLVED) continue;
-                if ((e & STAB_UNKNOWN) && !(e & STAB_CONST)) {
-                    sl[j] = UNRESOLVED;
-                } else {
+                if (!(e & STAB_UNKNOWN) || (e & STAB_CONST)) {
                     sl[j] = stab_slot(e);
                     cn[j] += stab_count(e);
+                } else if (sl[j] < NL) {  // the stitch met no chain: continue from its exit
+                    ps[j] = A.st[i].unk_exit[sl[j]];
+                    cn[j] += stab_count(e);
+                    sl[j] = NONE;
+                } else {  // entering off every chain: did the segment follow this position?
+                    const SegState* st = &A.st[i];
+                    const uint32_t nu = umin64(st->ures_n, NU);
+                    uint32_t v = STAB_UNKNOWN, f = 0;
+                    for (uint32_t u = 0; u < nu; u++)
+                        if (st->ures_pos[u] == ps[j]) { v = st->ures_val[u]; f = 1; ps[j] = st->ures_exit[u]; break; }
+                    if (!f) {
+                        sl[j] = UNRESOLVED;
+                    } else if (!(v & STAB_UNKNOWN)) {
+                        sl[j] = stab_slot(v);
+                        cn[j] += stab_count(v);
+                    } else {
+                        cn[j] += stab_count(v);  // still off every chain, at the new exit
+                    }
                 }
             }
         }
         GroupState* gs = reinterpret_cast<GroupState*>(A.groups) + g;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            gs->slot[lane + 32 * j] = sl[j];
+            gs->slot[lane + 32 * j] = sl[j] == NONE ? UNRESOLVED : sl[j];
             gs->count[lane + 32 * j] = cn[j];
         }
     }
