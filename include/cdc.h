@@ -172,11 +172,12 @@ CDC_API cdc_status cdc_get_option(cdc_handle h, cdc_option opt, int64_t* value);
 CDC_API cdc_status cdc_last_timing(cdc_handle h, float* summary_ms, float* chain_ms);
 
 /* Totals over the calls recorded since profiling was switched on or last
- * collected: number of calls, device milliseconds of the summary stage and of
- * the chain stage, and kernels launched. Synchronises on the recorded events
- * and clears them. Any output pointer may be NULL. */
+ * collected: number of calls, device milliseconds of the summary stage, of
+ * the chain stage, and of the speculation kernel alone (the first kernel of
+ * the chain stage; part of chain_ms), and kernels launched. Synchronises on
+ * the recorded events and clears them. Any output pointer may be NULL. */
 CDC_API cdc_status cdc_profile_collect(cdc_handle h, int* calls, double* summary_ms, double* chain_ms,
-                                       int64_t* launches);
+                                       double* spec_ms, int64_t* launches);
 
 /* Counters of the last call made with CDC_OPT_STATS on (up to n of them,
  * in this order): segments, single-thread chain steps, whole-warp chain steps

@@ -70,7 +70,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "cdc_last_timing": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)], i32),
             "cdc_last_launches": ([vp, ctypes.POINTER(i32)], i32),
             "cdc_profile_collect": ([vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
-                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)], i32),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(i64)], i32),
             "cdc_stats": ([vp, vp, i32, vp], i32),
             "cdc_chunk_static": ([i32, P, vp, sz, vp, ctypes.POINTER(sz), vp], i32),
             "cdc_status_string": ([i32], ctypes.c_char_p),
@@ -159,11 +160,12 @@ class Chunker:
         return n.value
 
     def profile_collect(self):
-        """(calls, summary ms, chain ms, kernel launches) recorded since the last collect."""
-        n, a, b, l = ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        """(calls, summary ms, chain ms, speculation-kernel ms, kernel launches)
+        recorded since the last collect."""
+        n, a, b, c, l = ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
         _check(self.lib.cdc_profile_collect(self.h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(b),
-                                            ctypes.byref(l)), "cdc_profile_collect")
-        return n.value, a.value, b.value, l.value
+                                            ctypes.byref(c), ctypes.byref(l)), "cdc_profile_collect")
+        return n.value, a.value, b.value, c.value, l.value
 
     # chunking
     def chunk(self, data, alg, w: int, mn: int, mx: int, out=None, stream=None):

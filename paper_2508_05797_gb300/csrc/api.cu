@@ -42,10 +42,10 @@ struct cdc_handle_s {
     // options
     int64_t seg = 0, span = 0, timeout_ms = 2000, force_bytes = 0, hold_item = -1, stats = 0, warp_chains = 0;
     // last-call bookkeeping
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // start, summaries done, end, speculation done
     bool timed = false;
     int launches = 0;
-    // profiling ring: event triples of up to PROF_CAP calls
+    // profiling ring: 4 events (as ev[]) for each of up to PROF_CAP calls
     static constexpr int PROF_CAP = 1024;
     int64_t profile = 0;
     cudaEvent_t* prof_ev = nullptr;
@@ -111,7 +111,7 @@ extern "C" cdc_status cdc_create(cdc_handle* out, int device) {
         cdc_destroy(h);
         return CDC_ERR_NOMEM;
     }
-    for (int i = 0; i < 3; i++) cudaEventCreate(&h->ev[i]);
+    for (int i = 0; i < 4; i++) cudaEventCreate(&h->ev[i]);
     *out = h;
     return CDC_OK;
 }
@@ -132,10 +132,10 @@ extern "C" cdc_status cdc_destroy(cdc_handle h) {
     cudaFree(h->host_stage);
     cudaFree(h->host_out);
     if (h->pinned_ctrl) cudaFreeHost(h->pinned_ctrl);
-    for (int i = 0; i < 3; i++)
+    for (int i = 0; i < 4; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     if (h->prof_ev) {
-        for (int i = 0; i < 3 * cdc_handle_s::PROF_CAP; i++) cudaEventDestroy(h->prof_ev[i]);
+        for (int i = 0; i < 4 * cdc_handle_s::PROF_CAP; i++) cudaEventDestroy(h->prof_ev[i]);
         free(h->prof_ev);
     }
     cudaGetLastError();
@@ -170,9 +170,9 @@ extern "C" cdc_status cdc_set_option(cdc_handle h, cdc_option opt, int64_t v) {
     case CDC_OPT_PROFILE:
         if (v && !h->prof_ev) {
             cudaSetDevice(h->device);
-            h->prof_ev = (cudaEvent_t*)calloc(3 * cdc_handle_s::PROF_CAP, sizeof(cudaEvent_t));
+            h->prof_ev = (cudaEvent_t*)calloc(4 * cdc_handle_s::PROF_CAP, sizeof(cudaEvent_t));
             if (!h->prof_ev) return CDC_ERR_NOMEM;
-            for (int i = 0; i < 3 * cdc_handle_s::PROF_CAP; i++)
+            for (int i = 0; i < 4 * cdc_handle_s::PROF_CAP; i++)
                 if (cudaEventCreate(&h->prof_ev[i]) != cudaSuccess) return CDC_ERR_CUDA;
         }
         h->profile = v ? 1 : 0;
@@ -316,7 +316,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     const bool rec = !capturing(st);
     h->timed = false;
     cudaEvent_t* ev = h->ev;
-    if (rec && h->profile && h->prof_n < cdc_handle_s::PROF_CAP) ev = h->prof_ev + 3 * h->prof_n++;
+    if (rec && h->profile && h->prof_n < cdc_handle_s::PROF_CAP) ev = h->prof_ev + 4 * h->prof_n++;
     if (batch) {
         if (launch_batch_setup(d_file_off, n_files, seg, h->item_off, h->item_file, h->scan_tmp, h->ctrl, st,
                                &h->launches) != cudaSuccess)
@@ -395,7 +395,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     if (gr.spec < 1) gr.spec = 1;
     if (gr.groups < 1) gr.groups = 1;
     if (gr.output < 1) gr.output = 1;
-    if (launch_chain(c, pl.rule, gr, st, &h->launches) != cudaSuccess) return CDC_ERR_CUDA;
+    if (launch_chain(c, pl.rule, gr, st, &h->launches, rec ? ev[3] : nullptr) != cudaSuccess) return CDC_ERR_CUDA;
     if (rec) {
         cudaEventRecord(ev[2], st);
         h->last_ev = ev;
@@ -559,21 +559,24 @@ extern "C" cdc_status cdc_last_launches(cdc_handle h, int* launches) {
 }
 
 extern "C" cdc_status cdc_profile_collect(cdc_handle h, int* calls, double* summary_ms, double* chain_ms,
-                                          int64_t* launches) {
+                                          double* spec_ms, int64_t* launches) {
     if (!h) return CDC_ERR_INVALID;
-    double a = 0, b = 0;
+    double a = 0, b = 0, c = 0;
     for (int i = 0; i < h->prof_n; i++) {
-        cudaEvent_t* ev = h->prof_ev + 3 * i;
+        cudaEvent_t* ev = h->prof_ev + 4 * i;
         if (cudaEventSynchronize(ev[2]) != cudaSuccess) return CDC_ERR_CUDA;
-        float x = 0, y = 0;
+        float x = 0, y = 0, z = 0;
         cudaEventElapsedTime(&x, ev[0], ev[1]);
         cudaEventElapsedTime(&y, ev[1], ev[2]);
+        cudaEventElapsedTime(&z, ev[1], ev[3]);
         a += x;
         b += y;
+        c += z;
     }
     if (calls) *calls = h->prof_n;
     if (summary_ms) *summary_ms = a;
     if (chain_ms) *chain_ms = b;
+    if (spec_ms) *spec_ms = c;
     if (launches) *launches = h->prof_launches;
     h->prof_n = 0;
     h->prof_launches = 0;

@@ -82,7 +82,9 @@ int chain_smem(int rule, uint32_t win);
 int spec_blocks_per_sm(int rule, uint32_t win);
 size_t seg_state_bytes();
 size_t group_state_bytes();
-cudaError_t launch_chain(const ChainLaunch& a, int rule, const ChainGrids& g, cudaStream_t st, int* launches);
+// ev_spec (may be null) is recorded on `st` right after the speculation kernel
+cudaError_t launch_chain(const ChainLaunch& a, int rule, const ChainGrids& g, cudaStream_t st, int* launches,
+                         cudaEvent_t ev_spec = nullptr);
 
 // batch set-up: item_off (n_files + 1), item_file, ctrl->n_items
 cudaError_t launch_batch_setup(const uint64_t* file_off, uint64_t n_files, uint64_t seg, uint64_t* item_off,

@@ -955,13 +955,15 @@ int chain_smem(int rule, uint32_t win) {
 }
 
 template <int RULE>
-static cudaError_t launch_rule(const ChainLaunch& a, const ChainGrids& gr, cudaStream_t st, int* launches) {
+static cudaError_t launch_rule(const ChainLaunch& a, const ChainGrids& gr, cudaStream_t st, int* launches,
+                               cudaEvent_t ev_spec) {
     int sm = chain_smem(RULE, a.win);
     cudaError_t e = cudaFuncSetAttribute(k_spec<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_output<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
     k_spec<RULE><<<gr.spec, NL, sm, st>>>(a);
+    if (ev_spec) cudaEventRecord(ev_spec, st);
     k_compose<RULE><<<gr.groups, 32, 0, st>>>(a);
     k_scan<RULE><<<1, 32, 0, st>>>(a);
     k_settle<RULE><<<gr.groups, 32, 0, st>>>(a);
@@ -970,14 +972,15 @@ static cudaError_t launch_rule(const ChainLaunch& a, const ChainGrids& gr, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_chain(const ChainLaunch& a, int rule, const ChainGrids& gr, cudaStream_t st, int* launches) {
+cudaError_t launch_chain(const ChainLaunch& a, int rule, const ChainGrids& gr, cudaStream_t st, int* launches,
+                         cudaEvent_t ev_spec) {
     switch (rule) {
-    case RULE_RAM: return launch_rule<RULE_RAM>(a, gr, st, launches);
-    case RULE_AE: return launch_rule<RULE_AE>(a, gr, st, launches);
-    case RULE_MAXP: return launch_rule<RULE_MAXP>(a, gr, st, launches);
-    case RULE_RAM_BYTES: return launch_rule<RULE_RAM_BYTES>(a, gr, st, launches);
-    case RULE_AE_BYTES: return launch_rule<RULE_AE_BYTES>(a, gr, st, launches);
-    default: return launch_rule<RULE_MAXP_BYTES>(a, gr, st, launches);
+    case RULE_RAM: return launch_rule<RULE_RAM>(a, gr, st, launches, ev_spec);
+    case RULE_AE: return launch_rule<RULE_AE>(a, gr, st, launches, ev_spec);
+    case RULE_MAXP: return launch_rule<RULE_MAXP>(a, gr, st, launches, ev_spec);
+    case RULE_RAM_BYTES: return launch_rule<RULE_RAM_BYTES>(a, gr, st, launches, ev_spec);
+    case RULE_AE_BYTES: return launch_rule<RULE_AE_BYTES>(a, gr, st, launches, ev_spec);
+    default: return launch_rule<RULE_MAXP_BYTES>(a, gr, st, launches, ev_spec);
     }
 }
 
