@@ -43,25 +43,48 @@ __global__ void k_reset(Ctrl* ctrl) {
     if (threadIdx.x == 0 && blockIdx.x == 0) reset_ctrl(ctrl);
 }
 
-// max and first argmax of one 16-byte chunk, as a key (max << 8) | (63 - pos)
-__device__ __forceinline__ uint32_t chunk_key(const uint32_t w[4], uint32_t q) {
-    uint32_t m = vmax4(vmax4(w[0], w[1]), vmax4(w[2], w[3]));
-    uint32_t M = hmax4(m), Mx = M * 0x01010101u;
-    uint32_t e0 = vcmpeq4(w[0], Mx), e1 = vcmpeq4(w[1], Mx), e2 = vcmpeq4(w[2], Mx), e3 = vcmpeq4(w[3], Mx);
-    uint32_t idx = e0 ? ((ffs32(e0) - 1) >> 3)
-                      : e1 ? 4 + ((ffs32(e1) - 1) >> 3) : e2 ? 8 + ((ffs32(e2) - 1) >> 3) : 12 + ((ffs32(e3) - 1) >> 3);
-    return (M << 8) | (63u - (16u * q + idx));
+// Maximum and first (LAST = false) or last (LAST = true) position of the
+// maximum of one 64-byte block held in shared memory, as the key
+// (max << 8) | tag, tag = 255 - position (first) or position (last).
+// Bytes go into 16-bit lanes next to their position tag with byte permutes,
+// so one native 16x2 max takes two bytes at a time and ties resolve to the
+// wanted end. The block's four 16-byte columns are read in the order
+// k ^ sw, which spreads a warp's reads over all shared-memory banks.
+// Bytes outside [lo, hi) count as 0 (after the complement `inv`).
+template <bool LAST>
+__device__ __forceinline__ uint32_t block_key(const uint8_t* blk, uint32_t sw, uint32_t inv, bool edge, uint64_t p0,
+                                              uint64_t lo, uint64_t hi) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint32_t c = (uint32_t)k ^ sw;
+        const uint4 v = *reinterpret_cast<const uint4*>(blk + 16 * c);
+        uint32_t w[4] = {v.x ^ inv, v.y ^ inv, v.z ^ inv, v.w ^ inv};
+        if (edge) mask16(w, p0 + 16 * c, lo, hi);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t base = 16u * c + 4u * (uint32_t)j;  // position of the word's byte 0
+            const uint32_t tag = LAST ? 0x03020100u + base * 0x01010101u : 0xFCFDFEFFu - base * 0x01010101u;
+            const uint32_t e = __byte_perm(w[j], tag, 0x2604);  // lanes (b0 << 8 | t0), (b2 << 8 | t2)
+            const uint32_t o = __byte_perm(w[j], tag, 0x3715);  // lanes (b1 << 8 | t1), (b3 << 8 | t3)
+            acc = __vmaxu2(acc, __vmaxu2(e, o));
+        }
+    }
+    return max(acc & 0xFFFFu, acc >> 16);
 }
 
-// last argmax key of one chunk for the block maximum M: (M << 8) | pos, or 0
-// when the chunk holds no byte equal to M
-__device__ __forceinline__ uint32_t chunk_key_last(const uint32_t w[4], uint32_t q, uint32_t M) {
-    uint32_t Mx = M * 0x01010101u;
-    uint32_t e0 = vcmpeq4(w[0], Mx), e1 = vcmpeq4(w[1], Mx), e2 = vcmpeq4(w[2], Mx), e3 = vcmpeq4(w[3], Mx);
-    if ((e0 | e1 | e2 | e3) == 0) return 0;
-    uint32_t idx = e3 ? 12 + ((31 - __clz(e3)) >> 3)
-                      : e2 ? 8 + ((31 - __clz(e2)) >> 3) : e1 ? 4 + ((31 - __clz(e1)) >> 3) : ((31 - __clz(e0)) >> 3);
-    return (M << 8) | (16u * q + idx);
+// Any byte at offsets [o0, o1] (inclusive) of a 64-byte block >= v (1 <= v <= 255):
+// bytes in 16-bit lanes, lane + (0x8000 - v) reaches bit 15 exactly when byte >= v.
+__device__ __forceinline__ bool block_any_geq(const uint8_t* blk, uint32_t o0, uint32_t o1, uint32_t v) {
+    const uint32_t K = (0x8000u - v) * 0x00010001u;
+    for (uint32_t q = o0 >> 2; q <= (o1 >> 2); q++) {
+        uint32_t x = *reinterpret_cast<const uint32_t*>(blk + 4 * q);
+        if (4 * q < o0) x &= 0xFFFFFFFFu << (8 * (o0 - 4 * q));
+        if (4 * q + 3 > o1) x &= 0xFFFFFFFFu >> (8 * (4 * q + 3 - o1));
+        const uint32_t e = __byte_perm(x, 0, 0x4240), o = __byte_perm(x, 0, 0x4341);
+        if (((e + K) | (o + K)) & 0x80008000u) return true;
+    }
+    return false;
 }
 
 // issue the copy of bytes [r0, r1) (physical positions) into the stage buffer
@@ -116,25 +139,21 @@ __global__ void __launch_bounds__(S1_THREADS) k_summary_max(SumLaunch a) {
         }
         const uint8_t* tb = buf + s * S1_TILE;
         const uint64_t T0 = t * S1_TILE;
-#pragma unroll
-        for (int it = 0; it < S1_TILE / 16 / S1_THREADS; it++) {
-            const uint32_t c = it * S1_THREADS + tid;  // 16-byte chunk in tile
-            uint4 v = reinterpret_cast<const uint4*>(tb)[c];
-            uint32_t w[4] = {v.x ^ inv, v.y ^ inv, v.z ^ inv, v.w ^ inv};
-            mask16(w, T0 + 16ull * c, a.lo, a.hi);
-            uint32_t key = chunk_key(w, c & 3u);
-            key = max(key, __shfl_xor_sync(FULL, key, 1));
-            key = max(key, __shfl_xor_sync(FULL, key, 2));
-            if ((c & 3u) == 0) {
-                uint64_t b = T0 / 64 + (c >> 2);
-                if (b < a.nblk) {
-                    a.smax[b] = (uint8_t)(key >> 8);
-                    a.sarg[b] = (uint8_t)(63u - (key & 0xFFu));
-                }
+        {
+            static_assert(S1_TILE / 64 == S1_THREADS, "one block of the tile per thread");
+            const uint32_t lb = (uint32_t)tid;
+            const uint64_t P0 = T0 + 64ull * lb;
+            const bool edge = P0 < a.lo || P0 + 64 > a.hi;
+            const uint32_t key = block_key<false>(tb + 64 * lb, (lb >> 1) & 3u, inv, edge, P0, a.lo, a.hi);
+            const uint32_t M = key >> 8;
+            const uint64_t b = T0 / 64 + lb;
+            if (b < a.nblk) {
+                a.smax[b] = (uint8_t)M;
+                a.sarg[b] = (uint8_t)(255u - (key & 0xFFu));
             }
-            // each iteration covers one 4 KiB superblock of the tile
-            uint32_t wm = __reduce_max_sync(FULL, key >> 8);
-            if ((tid & 31) == 0 && wm) atomicMax(&supmax[s][it], wm);
+            // 64 blocks (two warps) per 4 KiB superblock
+            const uint32_t wm = __reduce_max_sync(FULL, M);
+            if ((tid & 31) == 0 && wm) atomicMax(&supmax[s][lb >> 6], wm);
         }
         __syncthreads();  // every thread is done with stage s
         if (tid < S1_TILE / 4096) {
@@ -157,7 +176,7 @@ constexpr int MP_TILE_BLOCKS = 256;  // 16 KiB of targets per tile
 
 // Dynamic shared memory: 2 stages of (MP_TILE_BLOCKS + 2*hb) * 64 bytes, then
 // per-stage-block max / first / last arrays, then 2 mbarriers.
-__global__ void __launch_bounds__(MP_THREADS) k_summary_maxp(SumLaunch a) {
+__global__ void __launch_bounds__(MP_THREADS, 4) k_summary_maxp(SumLaunch a) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
     const uint32_t hb = a.halo_blocks;
@@ -214,32 +233,20 @@ __global__ void __launch_bounds__(MP_THREADS) k_summary_maxp(SumLaunch a) {
         const uint8_t* tb = buf + s * sbytes;
         const int64_t sb0 = (int64_t)(t * MP_TILE_BLOCKS) - (int64_t)hb;  // global block of stage block 0
         // 1) block max, first and last position of the max, for every stage block
-        for (uint32_t cb = 0; cb < nb * 4; cb += MP_THREADS) {
-            // every thread takes part in the shuffles; chunks past the stage are zeros
-            const uint32_t c = cb + tid;
-            const bool act = c < nb * 4;
-            uint4 v = act ? reinterpret_cast<const uint4*>(tb)[c] : make_uint4(0, 0, 0, 0);
-            uint32_t wd[4] = {v.x, v.y, v.z, v.w};
-            int64_t pos = (sb0 + (int64_t)(c >> 2)) * 64 + 16 * (int64_t)(c & 3u);
-            if (pos < 0 || (uint64_t)pos < a.lo || (uint64_t)pos + 16 > a.hi) {
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    if (pos < 0) wd[k] = 0;
-                    else wd[k] = clip_word(wd[k], ((uint64_t)pos >> 2) + k, a.lo, a.hi);
-                }
+        for (uint32_t sb = tid; sb < nb; sb += MP_THREADS) {
+            const int64_t gblk = sb0 + (int64_t)sb;
+            uint32_t kf = 0, kl = 0;
+            if (gblk >= 0) {  // blocks before position 0 stay all-zero
+                const uint64_t P0 = (uint64_t)gblk * 64;
+                const bool edge = P0 < a.lo || P0 + 64 > a.hi;
+                kf = block_key<false>(tb + 64 * sb, (sb >> 1) & 3u, 0u, edge, P0, a.lo, a.hi);
+                kl = block_key<true>(tb + 64 * sb, (sb >> 1) & 3u, 0u, edge, P0, a.lo, a.hi);
+            } else {
+                kf = 255u;  // max 0, first position 0
             }
-            uint32_t kf = chunk_key(wd, c & 3u);
-            kf = max(kf, __shfl_xor_sync(FULL, kf, 1));
-            kf = max(kf, __shfl_xor_sync(FULL, kf, 2));
-            uint32_t M = kf >> 8;
-            uint32_t kl = chunk_key_last(wd, c & 3u, M);
-            kl = max(kl, __shfl_xor_sync(FULL, kl, 1));
-            kl = max(kl, __shfl_xor_sync(FULL, kl, 2));
-            if (act && (c & 3u) == 0) {
-                bm[c >> 2] = (uint8_t)M;
-                bf[c >> 2] = (uint8_t)(63u - (kf & 0xFFu));
-                bl[c >> 2] = (uint8_t)(kl & 0xFFu);
-            }
+            bm[sb] = (uint8_t)(kf >> 8);
+            bf[sb] = (uint8_t)(255u - (kf & 0xFFu));
+            bl[sb] = (uint8_t)(kl & 0xFFu);
         }
         __syncthreads();
         // 2) target test, one thread per tile block
@@ -259,9 +266,7 @@ __global__ void __launch_bounds__(MP_THREADS) k_summary_maxp(SumLaunch a) {
                     const uint64_t blo = kb * 64, bhi = blo + 63;
                     if (blo >= wl && bhi <= wr) { ok = false; break; }
                     const uint64_t x0 = blo > wl ? blo : wl, x1 = bhi < wr ? bhi : wr;
-                    const uint8_t* sp = tb + (size_t)si * 64;
-                    for (uint64_t x = x0; x <= x1; x++)
-                        if (sp[x - blo] >= v) { ok = false; break; }
+                    if (block_any_geq(tb + (size_t)si * 64, (uint32_t)(x0 - blo), (uint32_t)(x1 - blo), v)) ok = false;
                 }
             }
             if (gb < a.nblk) a.smax[gb] = ok ? bf[sbi] : (uint8_t)0xFFu;
