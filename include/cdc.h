@@ -160,7 +160,7 @@ typedef enum {
     CDC_OPT_WARP_CHAINS = 7   /* speculative chains of a segment are stepped one
                                  per thread while more than this many are
                                  alive, then one per warp (all 32 lanes share
-                                 each step); 1..128, 0 = automatic (32) */
+                                 each step); 1..128, 0 = automatic (96) */
 } cdc_option;
 
 CDC_API cdc_status cdc_set_option(cdc_handle h, cdc_option opt, int64_t value);
@@ -183,7 +183,10 @@ CDC_API cdc_status cdc_profile_collect(cdc_handle h, int* calls, double* summary
  * in this order): segments, single-thread chain steps, whole-warp chain steps
  * in speculation, merged chains, stitch walks, stitch steps, uncovered table
  * entries, segments whose position hash filled, fallback walks in the
- * resolution, output steps, empty segments, chains handed to whole warps.
+ * resolution, output steps, empty segments, chains handed to whole warps,
+ * then clock cycles summed over segments (set-up, speculation, merge
+ * resolution, stitching), per-thread rounds, and the cycles of the rounds and
+ * of the one-warp-per-chain phase (19 counters in all).
  * Synchronises `stream`. */
 CDC_API cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream stream);
 
@@ -198,7 +201,8 @@ CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
  * cdc_chunk_static does what cdc_chunk does, on the CURRENT device, without a
  * handle and without allocating anything: no cudaMalloc / cudaFree, no
  * allocating library routine, no pinned host memory. Its scratch (block
- * summaries, per-segment speculation state, control block) is one fixed
+ * summaries, per-segment speculation state and position hashes, control
+ * block) is one fixed
  * array of CDC_STATIC_SCRATCH_BYTES in the library's device image, so it
  * serves inputs of at most CDC_STATIC_MAX_LEN bytes.
  *
@@ -223,7 +227,7 @@ CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
  *     wrong results. Serialise them.
  */
 #define CDC_STATIC_MAX_LEN ((size_t)16 << 20)
-#define CDC_STATIC_SCRATCH_BYTES ((size_t)2117632)
+#define CDC_STATIC_SCRATCH_BYTES ((size_t)10785280)
 
 CDC_API cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
                                     uint64_t* out_bounds, size_t* n, cdc_stream stream);

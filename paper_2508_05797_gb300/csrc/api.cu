@@ -27,6 +27,8 @@ struct cdc_handle_s {
     size_t st_cap = 0;      // bytes
     uint8_t* groups = nullptr;  // GroupState array
     size_t groups_cap = 0;      // bytes
+    uint8_t* hash = nullptr;    // per-segment position hashes
+    size_t hash_cap = 0;        // bytes
     Ctrl* ctrl = nullptr;
     uint64_t* item_off = nullptr;
     uint64_t* scan_tmp = nullptr;
@@ -124,6 +126,7 @@ extern "C" cdc_status cdc_destroy(cdc_handle h) {
     cudaFree(h->sarg);
     cudaFree(h->ssup);
     cudaFree(h->groups);
+    cudaFree(h->hash);
     cudaFree(h->st);
     cudaFree(h->ctrl);
     cudaFree(h->item_off);
@@ -303,6 +306,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
         if ((s = grow(&h->ssup, &h->ssup_cap, g.nsup + 64, false, st)) != CDC_OK) return s;
     }
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, st)) != CDC_OK) return s;
+    if ((s = grow(&h->hash, &h->hash_cap, items * seg_hash_bytes(), false, st)) != CDC_OK) return s;
     if ((s = grow(&h->groups, &h->groups_cap, ((items + GS - 1) / GS + 1) * group_state_bytes(), false, st)) !=
         CDC_OK)
         return s;
@@ -372,12 +376,13 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     c.bounds_index = bounds_index;
     c.d_count = d_count;
     c.st = reinterpret_cast<SegState*>(h->st);
+    c.hash = reinterpret_cast<unsigned long long*>(h->hash);
     c.groups = h->groups;
     c.ctrl = h->ctrl;
     c.timeout_ns = timeout_ns;
     c.hold_item = h->hold_item;
     c.stats = (int)h->stats;
-    c.warp_chains = h->warp_chains ? (uint32_t)h->warp_chains : 32u;
+    c.warp_chains = h->warp_chains ? (uint32_t)h->warp_chains : 96u;
     if (h->stats) cudaMemsetAsync(h->ctrl->stats, 0, sizeof(h->ctrl->stats), st);
     if (pl.sum != SUM_NONE) {
         const uint64_t mx4k = ((uint64_t)p.max + 4095) & ~4095ull;
@@ -390,9 +395,11 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     const uint64_t ngroups = (items + GS - 1) / GS;
     uint64_t gs = (uint64_t)h->sm_count * spec_blocks_per_sm(pl.rule, c.win);
     gr.spec = (int)(gs < items ? gs : items);
+    gr.stitch = (int)(items < (uint64_t)h->sm_count * 8 ? items : (uint64_t)h->sm_count * 8);
     gr.groups = (int)(ngroups < (uint64_t)h->sm_count * 16 ? ngroups : (uint64_t)h->sm_count * 16);
     gr.output = (int)(items < (uint64_t)h->sm_count * 32 ? items : (uint64_t)h->sm_count * 32);
     if (gr.spec < 1) gr.spec = 1;
+    if (gr.stitch < 1) gr.stitch = 1;
     if (gr.groups < 1) gr.groups = 1;
     if (gr.output < 1) gr.output = 1;
     if (launch_chain(c, pl.rule, gr, st, &h->launches, rec ? ev[3] : nullptr) != cudaSuccess) return CDC_ERR_CUDA;
@@ -524,6 +531,7 @@ extern "C" cdc_status cdc_reserve(cdc_handle h, cdc_alg alg, cdc_params p, size_
     }
     if (pl.sum != SUM_NONE && (s = grow(&h->ssup, &h->ssup_cap, len / 4096 + 66, false, 0)) != CDC_OK) return s;
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, 0)) != CDC_OK) return s;
+    if ((s = grow(&h->hash, &h->hash_cap, items * seg_hash_bytes(), false, 0)) != CDC_OK) return s;
     if ((s = grow(&h->groups, &h->groups_cap, ((items + GS - 1) / GS + 1) * group_state_bytes(), false, 0)) !=
         CDC_OK)
         return s;
@@ -591,7 +599,7 @@ extern "C" cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream s
     if (cudaMemcpyAsync(h->pinned_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return CDC_ERR_CUDA;
-    for (int i = 0; i < n && i < 16; i++) out[i] = h->pinned_ctrl->stats[i];
+    for (int i = 0; i < n && i < STAT_N; i++) out[i] = h->pinned_ctrl->stats[i];
     return CDC_OK;
 }
 
@@ -600,7 +608,7 @@ extern "C" cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream s
 // Same plan, kernels and launch order as run() for a single stream, but every
 // workspace pointer points into g_fixed_scratch, so nothing is allocated.
 // Layout (byte offsets, each part 256-byte aligned):
-//   control block | smax | sarg | ssup | segment states | group states
+//   control block | smax | sarg | ssup | segment states | group states | segment hashes
 
 namespace {
 constexpr uint64_t round256(uint64_t x) { return (x + 255) & ~255ull; }
@@ -611,8 +619,9 @@ constexpr uint64_t kFixBlocks = ((kFixMaxLen + 63 + 63) / 64 + 15) & ~15ull;
 constexpr uint64_t kFixSumBytes = round256(kFixBlocks + 64);
 constexpr uint64_t kFixSupBytes = round256((kFixMaxLen + 63 + 4095) / 4096 + 64);
 constexpr uint64_t kFixItems = kFixMaxLen / kFixMinSeg + 1;
-constexpr uint64_t kFixSegSlot = 3072;    // >= sizeof(SegState), checked at set-up
+constexpr uint64_t kFixSegSlot = 3584;    // >= sizeof(SegState), checked at set-up
 constexpr uint64_t kFixGroupSlot = 2048;  // >= sizeof(GroupState), checked at set-up
+constexpr uint64_t kFixHashSlot = 16384;  // >= a segment's position hash, checked at set-up
 constexpr uint64_t kFixGroups = kFixItems / GS + 2;
 constexpr uint64_t kFixCtrlBytes = 256;
 constexpr uint64_t kFixOffSmax = kFixCtrlBytes;
@@ -620,7 +629,8 @@ constexpr uint64_t kFixOffSarg = kFixOffSmax + kFixSumBytes;
 constexpr uint64_t kFixOffSup = kFixOffSarg + kFixSumBytes;
 constexpr uint64_t kFixOffSt = kFixOffSup + kFixSupBytes;
 constexpr uint64_t kFixOffGroups = kFixOffSt + kFixItems * kFixSegSlot;
-constexpr uint64_t kFixTotal = kFixOffGroups + kFixGroups * kFixGroupSlot;
+constexpr uint64_t kFixOffHash = kFixOffGroups + kFixGroups * kFixGroupSlot;
+constexpr uint64_t kFixTotal = kFixOffHash + kFixItems * kFixHashSlot;
 static_assert(kFixTotal == CDC_STATIC_SCRATCH_BYTES, "scratch layout and header disagree");
 static_assert(sizeof(Ctrl) <= kFixCtrlBytes, "control block does not fit");
 constexpr int kFixMaxDevices = 64;
@@ -638,7 +648,8 @@ static cdc_status fixed_scratch(int dev, cudaStream_t st, uint8_t** out) {
     if (dev < 0 || dev >= kFixMaxDevices) return CDC_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_fixed_mu);
     if (!g_fixed_ptr[dev]) {
-        if (seg_state_bytes() > kFixSegSlot || group_state_bytes() > kFixGroupSlot) return CDC_ERR_INTERNAL;
+        if (seg_state_bytes() > kFixSegSlot || group_state_bytes() > kFixGroupSlot || seg_hash_bytes() > kFixHashSlot)
+            return CDC_ERR_INTERNAL;
         uint8_t* p = nullptr;
         if (cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_fixed_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
@@ -725,11 +736,12 @@ extern "C" cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t*
     c.out = out_bounds;
     c.capacity = *n;
     c.st = reinterpret_cast<SegState*>(scr + kFixOffSt);
+    c.hash = reinterpret_cast<unsigned long long*>(scr + kFixOffHash);
     c.groups = scr + kFixOffGroups;
     c.ctrl = ctrl;
     c.timeout_ns = timeout_ns;
     c.hold_item = -1;
-    c.warp_chains = 32u;
+    c.warp_chains = 96u;
     if (pl.sum != SUM_NONE) {
         const uint64_t mx4k = ((uint64_t)p.max + 4095) & ~4095ull;
         c.quiet_run = pl.sum == SUM_MAXP ? (uint32_t)(p.max / 8192 > 1 ? p.max / 8192 : 1) : 1u;
@@ -741,9 +753,11 @@ extern "C" cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t*
     const uint64_t ngroups = (items + GS - 1) / GS;
     const uint64_t gs = (uint64_t)cfg.sm_count * spec_blocks_per_sm(pl.rule, c.win);
     gr.spec = (int)(gs < items ? gs : items);
+    gr.stitch = (int)(items < (uint64_t)cfg.sm_count * 8 ? items : (uint64_t)cfg.sm_count * 8);
     gr.groups = (int)(ngroups < (uint64_t)cfg.sm_count * 16 ? ngroups : (uint64_t)cfg.sm_count * 16);
     gr.output = (int)(items < (uint64_t)cfg.sm_count * 32 ? items : (uint64_t)cfg.sm_count * 32);
     if (gr.spec < 1) gr.spec = 1;
+    if (gr.stitch < 1) gr.stitch = 1;
     if (gr.groups < 1) gr.groups = 1;
     if (gr.output < 1) gr.output = 1;
     if (launch_chain(c, pl.rule, gr, st, &launches) != cudaSuccess) return CDC_ERR_CUDA;

@@ -20,7 +20,7 @@ struct Ctrl {
     unsigned int err;            // sticky error bits, cleared by the host
     unsigned int stats_on;       // 1: kernels accumulate the counters below
     unsigned int pad[5];
-    unsigned long long stats[16];  // see STAT_* (reset by the host)
+    unsigned long long stats[22];  // see STAT_* (reset by the host)
 };
 enum : int {
     STAT_SEGMENTS = 0,      // non-empty segments speculated
@@ -38,7 +38,14 @@ enum : int {
     STAT_CYC_SETUP = 12,    // cycles (summed over CTAs): bounds + staging
     STAT_CYC_THREADS = 13,  //   per-thread speculation rounds
     STAT_CYC_WARPS = 14,    //   whole-warp survivors + merge resolution
-    STAT_CYC_STITCH = 15    //   waiting for the predecessor + stitching
+    STAT_CYC_STITCH = 15,   //   waiting for the predecessor + stitching
+    STAT_ROUNDS = 16,       // per-thread rounds (summed over segments)
+    STAT_CYC_ROUNDS = 17,   //   their cycles (part of STAT_CYC_THREADS)
+    STAT_CYC_SURV = 18,     // cycles of the one-warp-per-chain phase (part of STAT_CYC_THREADS)
+    STAT_CYC_WSTEP = 19,    // cycles inside whole-warp chain steps of that phase (summed over steps)
+    STAT_CYC_WHASH = 20,    // cycles of their position-hash inserts
+    STAT_PROBES = 21,       // hash slots probed by those inserts
+    STAT_N = 22
 };
 enum : unsigned int { ERR_TIMEOUT = 1u, ERR_INTERNAL = 2u };
 

@@ -59,6 +59,7 @@ struct ChainLaunch {
     uint64_t* d_count;       // receives the total, may be NULL
     // workspace
     SegState* st;
+    unsigned long long* hash;  // per segment: its position hash (seg_hash_bytes())
     void* groups;            // GroupState per GS segments
     Ctrl* ctrl;
     uint64_t timeout_ns;
@@ -76,11 +77,12 @@ cudaError_t launch_summary(const SumLaunch& a, int kind, int grid, cudaStream_t 
 cudaError_t launch_reset(Ctrl* ctrl, cudaStream_t st);
 
 struct ChainGrids {
-    int spec, groups, output;
+    int spec, stitch, groups, output;
 };
 int chain_smem(int rule, uint32_t win);
 int spec_blocks_per_sm(int rule, uint32_t win);
 size_t seg_state_bytes();
+size_t seg_hash_bytes();
 size_t group_state_bytes();
 // ev_spec (may be null) is recorded on `st` right after the speculation kernel
 cudaError_t launch_chain(const ChainLaunch& a, int rule, const ChainGrids& g, cudaStream_t st, int* launches,

@@ -47,12 +47,12 @@ constexpr int NU = 8;  // uncovered positions resolved per segment
 
 struct __align__(128) SegState {
     unsigned long long X[NL];         // chain exits (first position >= seg_hi), ~0 if idle
+    unsigned int cnt[NL];             // boundaries of each chain inside the segment
     unsigned int table[NL];           // predecessor chain -> (chain, count)
     unsigned long long unk_exit[NL];  // exit of the followed chain for UNKNOWN entries
     unsigned long long seg_lo, seg_hi, flo, fhi;
     unsigned int geo;                 // bit0 first of file, bit1 last of file, bit2 empty
-    unsigned int flagA;               // X and geometry published
-    unsigned int flagB;               // table and unk_exit published
+    unsigned int flagA;               // X, counts, geometry and hash published
     unsigned int ures_n;              // entries of ures_* below
     // positions that reach this segment off every chain (the nearest non-empty
     // predecessor's uncovered exits), each followed here like a stitch walk
@@ -152,15 +152,19 @@ __device__ Geo seg_geo(const ChainLaunch& A, uint64_t item) {
 constexpr int HSLOTS = 2048;
 constexpr int HFILL = 1400;  // stop inserting beyond this many entries
 
+size_t seg_hash_bytes() { return (size_t)HSLOTS * sizeof(unsigned long long); }
+
 __device__ __forceinline__ uint32_t hslot(uint32_t key) { return (key * 2654435761u) >> 21; }  // 11 bits
 constexpr uint32_t H_INSERTED = 0xFFFFFFFFu, H_FULL = 0xFFFFFFFEu;
 
 // insert; returns H_INSERTED, H_FULL, or the value already stored for key
-__device__ __forceinline__ uint32_t hinsert(unsigned long long* ht, unsigned int* fill, uint32_t key, uint32_t val) {
+__device__ __forceinline__ uint32_t hinsert(unsigned long long* ht, unsigned int* fill, uint32_t key, uint32_t val,
+                                            uint32_t* probes = nullptr) {
     if (*reinterpret_cast<volatile unsigned int*>(fill) >= (unsigned)HFILL) return H_FULL;
     const unsigned long long ent = ((unsigned long long)key << 32) | val;
     uint32_t s = hslot(key);
     for (int i = 0; i < 64; i++) {
+        if (probes) (*probes)++;
         unsigned long long prev = atomicCAS(&ht[s], 0ull, ent);
         if (prev == 0ull) {
             atomicAdd(fill, 1u);
@@ -224,7 +228,6 @@ struct SpecShared {
     unsigned int mi[NL];   // index of that position in the target chain
     unsigned long long geo[5];
     unsigned long long item;
-    unsigned long long qitem;  // nearest non-empty predecessor
     int ok;
 };
 
@@ -290,10 +293,10 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
         uint32_t c = 0;
         int mg = -1;
         uint32_t mi = 0;
+        long long t_surv0 = 0;
         if (empty) {
-            // nothing inside: the predecessor's exits pass through unchanged
-            if (!wait_flag_thread(&A.st[item - 1].flagA, epoch, A, item)) sh.ok = 0;
-            else x = A.st[item - 1].X[tid];
+            // nothing inside: the nearest non-empty predecessor's exits pass
+            // through unchanged (copied by the stitch kernel)
         } else {
             uint64_t start = ~0ull;
             if (first) {
@@ -319,9 +322,12 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
             __syncthreads();
             int buf = 0;
             const bool rec = !first;
+            const long long t_r0 = clock64();
+            uint32_t rounds = 0;
             for (;;) {
                 const unsigned nq = sh.nq;
                 if (nq <= A.warp_chains) break;  // the rest: one warp per chain
+                rounds++;
                 if (tid == 0) sh.nq2 = 0;
                 __syncthreads();
                 if ((unsigned)tid < nq) {
@@ -369,6 +375,12 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                 buf ^= 1;
                 __syncthreads();
             }
+            const long long t_r1 = clock64();
+            t_surv0 = t_r1;
+            if (A.stats && tid == 0) {
+                stat_add(A, STAT_ROUNDS, rounds);
+                stat_add(A, STAT_CYC_ROUNDS, (unsigned long long)(t_r1 - t_r0));
+            }
             if (A.stats) {
                 unsigned long long tot = tsteps;
                 for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULL, tot, o);
@@ -388,11 +400,15 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                 int qmg = -1;
                 uint32_t qmi = 0;
                 while (v < seg_hi) {
+                    const long long c0 = A.stats ? clock64() : 0;
                     if (recq) {
                         uint32_t hr = H_FULL;
+                        uint32_t probes = 0;
                         if (lane == 0 && cc < 0xFFFFu)
-                            hr = hinsert(sh.ht, &sh.fill, (uint32_t)(v - seg_lo) + 1u, (l << 16) | cc);
+                            hr = hinsert(sh.ht, &sh.fill, (uint32_t)(v - seg_lo) + 1u, (l << 16) | cc, &probes);
                         hr = __shfl_sync(FULL, hr, 0);
+                        if (A.stats && lane == 0) stat_add(A, STAT_PROBES, probes);
+                        if (A.stats && lane == 0) stat_add(A, STAT_CYC_WHASH, (unsigned long long)(clock64() - c0));
                         if (hr == H_FULL) {
                             recq = false;
                         } else if (hr != H_INSERTED) {
@@ -403,9 +419,11 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                     }
                     uint32_t k;
                     uint64_t dd;
+                    const long long c1 = A.stats ? clock64() : 0;
                     v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
                     cc += k;
                     if (lane == 0) stat_add(A, STAT_WARP_STEPS, 1);
+                    if (A.stats && lane == 0) stat_add(A, STAT_CYC_WSTEP, (unsigned long long)(clock64() - c1));
                 }
                 if (lane == 0) {
                     sh.mg[l] = qmg;
@@ -425,6 +443,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
             if (tid == 0) stat_add(A, STAT_EMPTY, 1);
         }
         __syncthreads();
+        if (A.stats && tid == 0 && !empty) stat_add(A, STAT_CYC_SURV, (unsigned long long)(clock64() - t_surv0));
         lap(STAT_CYC_THREADS);
         __syncthreads();
         mg = sh.mg[tid];
@@ -441,11 +460,16 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
             c = acc + sh.cnt[l];
         }
         __syncthreads();
-        sh.X[tid] = x;
-        sh.cnt[tid] = c;
         me->X[tid] = x;
+        me->cnt[tid] = c;
         if (tid == 0) {
             me->seg_lo = seg_lo; me->seg_hi = seg_hi; me->flo = flo; me->fhi = fhi; me->geo = geo;
+        }
+        // the position hash goes to HBM for the stitch kernels
+        if (!first && !empty) {
+            uint4* dst = reinterpret_cast<uint4*>(A.hash + item * (uint64_t)HSLOTS);
+            const uint4* src = reinterpret_cast<const uint4*>(sh.ht);
+            for (int i = tid; i < HSLOTS / 2; i += NL) dst[i] = src[i];
         }
         __syncthreads();
         if (!sh.ok) break;
@@ -454,56 +478,119 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
             if (!hold) st_release(&me->flagA, epoch);
         }
         lap(STAT_CYC_WARPS);
+    }
+}
 
-        // Follow the chain from e (every lane of the warp computes the same
-        // steps) until it lands on a hashed position of a chain of this
-        // segment, or reaches seg_hi. Returns the table encoding; *ux receives
-        // the exit when no chain was met (0 otherwise).
-        auto stitch_walk = [&](uint64_t e, uint64_t* ux) -> uint32_t {
-            uint64_t v = e;
-            uint32_t ne = 0, res = STAB_UNKNOWN;
-            while (v < seg_hi) {
-                const uint32_t hv = hfind(sh.ht, (uint32_t)(v - seg_lo) + 1u);
-                if (hv != ~0u) {
-                    const uint32_t m = hv >> 16, idx = hv & 0xFFFFu;
-                    res = stab_enc(m, ne + sh.cnt[m] - idx + (last ? 1u : 0u));
-                    break;
-                }
-                uint32_t k;
-                uint64_t dd;
-                v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
-                ne += k;
-                if (lane == 0) stat_add(A, STAT_STITCH_STEPS, 1);
-            }
-            *ux = 0;
-            if (res == STAB_UNKNOWN) {
-                // ended at or past seg_hi: does it end on one of the chains' exits?
-                int m = -1;
-                for (int j = 0; j < NL && m < 0; j++)
-                    if (sh.X[j] == v) m = j;
-                res = m >= 0 ? stab_enc((uint32_t)m, ne + (last ? 1u : 0u))
-                             : (STAB_UNKNOWN | ((ne + (last ? 1u : 0u)) & 0x7FFFFFu));
-                *ux = v;
-            }
-            if (lane == 0) {
-                stat_add(A, STAT_STITCH_WALKS, 1);
-                if (res & STAB_UNKNOWN) stat_add(A, STAT_UNKNOWN, 1);
-            }
-            return res;
-        };
+// ---- stitching (after every segment has speculated: no waits) --------------------
 
-        // ---- stitching table: predecessor chain tid -> (chain, count)
+// Nearest non-empty segment before `item` in its file (empty segments pass
+// positions and chains through unchanged). item is not the first of its file.
+__device__ __forceinline__ uint64_t nonempty_pred(const ChainLaunch& A, uint64_t item) {
+    uint64_t q = item - 1;
+    while (q > 0 && (A.st[q].geo & GEO_EMPTY) && !(A.st[q].geo & GEO_FIRST)) q--;
+    return q;
+}
+
+// Follow the chain from e (every lane of the warp computes the same steps)
+// until it lands on a hashed position of a chain of this segment, or reaches
+// seg_hi. Returns the table encoding; *ux receives the exit when no chain was
+// met (0 otherwise). ht, X, cnt: this segment's hash, exits and counts.
+template <int RULE>
+__device__ uint32_t stitch_walk(const ChainLaunch& A, const SumView& S, const RawView& R, const Prm& P,
+                                const unsigned long long* ht, const unsigned long long* X, const unsigned int* cnt,
+                                uint64_t seg_lo, uint64_t seg_hi, uint64_t flo, uint64_t fhi, bool last, uint64_t e,
+                                uint64_t* ux) {
+    const int lane = threadIdx.x & 31;
+    uint64_t v = e;
+    uint32_t ne = 0, res = STAB_UNKNOWN;
+    while (v < seg_hi) {
+        const uint32_t hv = hfind(ht, (uint32_t)(v - seg_lo) + 1u);
+        if (hv != ~0u) {
+            const uint32_t m = hv >> 16, idx = hv & 0xFFFFu;
+            res = stab_enc(m, ne + cnt[m] - idx + (last ? 1u : 0u));
+            break;
+        }
+        uint32_t k;
+        uint64_t dd;
+        v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+        ne += k;
+        if (lane == 0) stat_add(A, STAT_STITCH_STEPS, 1);
+    }
+    *ux = 0;
+    if (res == STAB_UNKNOWN) {
+        // ended at or past seg_hi: does it end on one of the chains' exits?
+        uint32_t found = NL;
+#pragma unroll
+        for (int j = 0; j < NL / 32; j++) {
+            const uint32_t b = __ballot_sync(FULL, X[j * 32 + lane] == v);
+            if (b && found == NL) found = (uint32_t)(j * 32 + __ffs((int)b) - 1);
+        }
+        res = found < NL ? stab_enc(found, ne + (last ? 1u : 0u))
+                         : (STAB_UNKNOWN | ((ne + (last ? 1u : 0u)) & 0x7FFFFFu));
+        *ux = v;
+    }
+    if (lane == 0) {
+        stat_add(A, STAT_STITCH_WALKS, 1);
+        if (res & STAB_UNKNOWN) stat_add(A, STAT_UNKNOWN, 1);
+    }
+    return res;
+}
+
+struct StitchShared {
+    unsigned long long ht[HSLOTS];
+    unsigned long long X[NL];
+    unsigned int cnt[NL];
+    int ok;
+};
+
+// Load a segment's hash, exits and counts into shared memory.
+__device__ __forceinline__ void load_segment(const ChainLaunch& A, uint64_t item, StitchShared& sh) {
+    const int tid = threadIdx.x;
+    const uint4* src = reinterpret_cast<const uint4*>(A.hash + item * (uint64_t)HSLOTS);
+    uint4* dst = reinterpret_cast<uint4*>(sh.ht);
+    for (int i = tid; i < HSLOTS / 2; i += NL) dst[i] = src[i];
+    sh.X[tid] = A.st[item].X[tid];
+    sh.cnt[tid] = A.st[item].cnt[tid];
+}
+
+// k_stitch: table "predecessor chain -> (chain, boundaries in this segment)"
+// for every segment; empty segments take their predecessor's exits.
+template <int RULE>
+__global__ void __launch_bounds__(NL) k_stitch(ChainLaunch A) {
+    __shared__ StitchShared sh;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t epoch = ld_volatile(&A.ctrl->epoch);
+    const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
+                                           : A.n_items;
+    const Prm P{A.w, A.mn, A.mx};
+    const RawView R{A.base, A.inv};
+    const SumView S{A.smax, A.sarg, nullptr, nullptr, 0, 0, A.ssup};
+    for (uint64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const long long t0 = clock64();
+        if (tid == 0) {
+            sh.ok = ld_volatile(&A.ctrl->err) == 0;
+            // every segment published its state before this kernel started,
+            // unless a test holds one back: then this bounded wait runs out
+            if (sh.ok && !wait_flag_thread(&A.st[item].flagA, epoch, A, item)) sh.ok = 0;
+        }
+        __syncthreads();
+        if (!sh.ok) break;
+        SegState* me = &A.st[item];
+        const uint32_t geo = me->geo;
+        const bool first = geo & GEO_FIRST, last = geo & GEO_LAST, empty = geo & GEO_EMPTY;
         uint32_t tab;
         unsigned long long unk = 0;
         if (first) {
-            tab = stab_enc(0, sh.cnt[0] - 1 + (last ? 1u : 0u)) | STAB_CONST;
+            tab = stab_enc(0, me->cnt[0] - 1 + (last ? 1u : 0u)) | STAB_CONST;
         } else if (empty) {
             tab = stab_enc((uint32_t)tid, 0);
+            me->X[tid] = A.st[nonempty_pred(A, item)].X[tid];
         } else {
-            if (tid == 0 && !wait_flag_thread(&A.st[item - 1].flagA, epoch, A, item)) sh.ok = 0;
+            const uint64_t p = nonempty_pred(A, item);
+            const uint64_t xp = A.st[p].X[tid];
+            load_segment(A, item, sh);
             __syncthreads();
-            if (!sh.ok) break;
-            const uint64_t xp = A.st[item - 1].X[tid];
+            const uint64_t seg_lo = me->seg_lo, seg_hi = me->seg_hi, flo = me->flo, fhi = me->fhi;
             tab = STAB_UNKNOWN;
             uint32_t todo = __ballot_sync(FULL, xp != ~0ull);
             while (todo) {
@@ -511,7 +598,8 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                 const uint64_t e = __shfl_sync(FULL, xp, ld);
                 const uint32_t same = __ballot_sync(FULL, xp == e) & todo;
                 uint64_t ux;
-                const uint32_t res = stitch_walk(e, &ux);
+                const uint32_t res = stitch_walk<RULE>(A, S, R, P, sh.ht, sh.X, sh.cnt, seg_lo, seg_hi, flo, fhi,
+                                                       last, e, &ux);
                 if ((same >> lane) & 1u) {
                     tab = res;
                     unk = ux;
@@ -522,31 +610,53 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
         me->table[tid] = tab;
         me->unk_exit[tid] = unk;
         __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            if (!hold) st_release(&me->flagB, epoch);
-        }
+        if (A.stats && tid == 0) stat_add(A, STAT_CYC_STITCH, (unsigned long long)(clock64() - t0));
+    }
+}
 
-        // ---- uncovered exits of the nearest non-empty predecessor (empty
-        // segments pass positions through unchanged): follow each distinct one
-        // here, so that the resolution kernels need not walk this segment
-        if (tid == 0) {
-            uint64_t q = item - 1;  // flagA of item - 1 implies flagA of the empty run before it
-            if (!first && !empty) {
-                while (q > 0 && (A.st[q].geo & GEO_EMPTY) && !(A.st[q].geo & GEO_FIRST)) q--;
-                if (!wait_flag_thread(&A.st[q].flagB, epoch, A, item)) sh.ok = 0;
-            }
-            sh.qitem = q;
+// k_ures: positions that reach a segment off every chain (its nearest
+// non-empty predecessor's uncovered exits) are followed here, so that the
+// resolution kernels need not walk whole segments.
+template <int RULE>
+__global__ void __launch_bounds__(NL) k_ures(ChainLaunch A) {
+    __shared__ StitchShared sh;
+    __shared__ int any;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
+                                           : A.n_items;
+    if (ld_volatile(&A.ctrl->err)) return;
+    const Prm P{A.w, A.mn, A.mx};
+    const RawView R{A.base, A.inv};
+    const SumView S{A.smax, A.sarg, nullptr, nullptr, 0, 0, A.ssup};
+    for (uint64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        SegState* me = &A.st[item];
+        const uint32_t geo = me->geo;
+        const bool first = geo & GEO_FIRST, last = geo & GEO_LAST, empty = geo & GEO_EMPTY;
+        if (first || empty) {
+            if (tid == 0) me->ures_n = 0;
+            continue;
         }
+        const SegState* qs = &A.st[nonempty_pred(A, item)];
+        const uint32_t t = qs->table[tid];
+        const bool u = (t & STAB_UNKNOWN) && !(t & STAB_CONST);
+        if (tid == 0) any = 0;
         __syncthreads();
-        if (!sh.ok) break;
-        if (!first && !empty && tid < 32) {
-            const SegState* qs = &A.st[sh.qitem];
+        if (u) any = 1;
+        __syncthreads();
+        if (!any) {
+            if (tid == 0) me->ures_n = 0;
+            __syncthreads();
+            continue;
+        }
+        load_segment(A, item, sh);
+        __syncthreads();
+        if (tid < 32) {
+            const uint64_t seg_lo = me->seg_lo, seg_hi = me->seg_hi, flo = me->flo, fhi = me->fhi;
             uint64_t up[NL / 32];
 #pragma unroll
             for (int j = 0; j < NL / 32; j++) {
-                const uint32_t t = qs->table[lane + 32 * j];
-                up[j] = ((t & STAB_UNKNOWN) && !(t & STAB_CONST)) ? qs->unk_exit[lane + 32 * j] : ~0ull;
+                const uint32_t tj = qs->table[lane + 32 * j];
+                up[j] = ((tj & STAB_UNKNOWN) && !(tj & STAB_CONST)) ? qs->unk_exit[lane + 32 * j] : ~0ull;
             }
             uint32_t nu = 0;
             for (int j = 0; j < NL / 32; j++) {
@@ -554,13 +664,13 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                 while (todo && nu < (uint32_t)NU) {
                     const int ld = __ffs((int)todo) - 1;
                     const uint64_t e = __shfl_sync(FULL, up[j], ld);
-                    // drop e everywhere (it may repeat in later words too)
 #pragma unroll
                     for (int jj = 0; jj < NL / 32; jj++)
                         if (up[jj] == e) up[jj] = ~0ull;
                     todo = __ballot_sync(FULL, up[j] != ~0ull);
                     uint64_t ux;
-                    const uint32_t res = stitch_walk(e, &ux);
+                    const uint32_t res = stitch_walk<RULE>(A, S, R, P, sh.ht, sh.X, sh.cnt, seg_lo, seg_hi, flo, fhi,
+                                                           last, e, &ux);
                     if (lane == 0) {
                         me->ures_pos[nu] = e;
                         me->ures_exit[nu] = ux;
@@ -570,11 +680,8 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                 }
             }
             if (lane == 0) me->ures_n = nu;
-        } else if (tid == 0) {
-            me->ures_n = 0;
         }
         __syncthreads();
-        lap(STAT_CYC_STITCH);
     }
 }
 
@@ -964,11 +1071,13 @@ static cudaError_t launch_rule(const ChainLaunch& a, const ChainGrids& gr, cudaS
     if (e != cudaSuccess) return e;
     k_spec<RULE><<<gr.spec, NL, sm, st>>>(a);
     if (ev_spec) cudaEventRecord(ev_spec, st);
+    k_stitch<RULE><<<gr.stitch, NL, 0, st>>>(a);
+    k_ures<RULE><<<gr.stitch, NL, 0, st>>>(a);
     k_compose<RULE><<<gr.groups, 32, 0, st>>>(a);
     k_scan<RULE><<<1, 32, 0, st>>>(a);
     k_settle<RULE><<<gr.groups, 32, 0, st>>>(a);
     k_output<RULE><<<gr.output, 32, sm, st>>>(a);
-    *launches += 5;
+    *launches += 7;
     return cudaGetLastError();
 }
 

@@ -30,8 +30,10 @@
 
 #if defined(__CUDACC__)
 #define CDC_HD __host__ __device__ __forceinline__
+#define CDC_UNROLL _Pragma("unroll")
 #else
 #define CDC_HD inline
+#define CDC_UNROLL
 #endif
 
 namespace cdc {
@@ -93,9 +95,59 @@ CDC_HD uint32_t hmax4(uint32_t v) {
     return v & 0xFFu;
 }
 
+// ---- bytes in 16-bit lanes: a word's bytes 0 and 2 ("even") and 1 and 3
+// ("odd") each go into the low half of a 16-bit lane, where native 16x2
+// integer operations handle two bytes at a time.
+CDC_HD uint32_t vmax2(uint32_t a, uint32_t b) {
+#if defined(__CUDA_ARCH__)
+    return __vmaxu2(a, b);
+#else
+    uint32_t lo = (a & 0xFFFFu) > (b & 0xFFFFu) ? (a & 0xFFFFu) : (b & 0xFFFFu);
+    uint32_t hi = (a >> 16) > (b >> 16) ? (a >> 16) : (b >> 16);
+    return lo | (hi << 16);
+#endif
+}
+
+// running maximum of the bytes of the words added
+struct ByteMax {
+    uint32_t e = 0, o = 0;
+    CDC_HD void add(uint32_t x) {
+        e = vmax2(e, x & 0x00FF00FFu);
+        o = vmax2(o, (x >> 8) & 0x00FF00FFu);
+    }
+    CDC_HD uint32_t get() const {
+        const uint32_t m = vmax2(e, o);
+        return (m & 0xFFFFu) > (m >> 16) ? (m & 0xFFFFu) : (m >> 16);
+    }
+    // some byte is 255: the maximum cannot grow
+    CDC_HD bool full() const { return ((vmax2(e, o) + 0x00010001u) & 0x01000100u) != 0; }
+};
+
+// Lane offset K for ge_flags(): (0x8000 - M) in both 16-bit lanes, 1 <= M <= 255.
+CDC_HD uint32_t ge_key(uint32_t M) { return (0x8000u - M) * 0x00010001u; }
+
+// Bit 7 of byte k is set where byte k of x is >= M (K = ge_key(M)): a byte
+// plus 0x8000 - M reaches bit 15 of its lane exactly when it is >= M, and no
+// lane overflows into the next.
+CDC_HD uint32_t ge_flags(uint32_t x, uint32_t K) {
+    const uint32_t e = (x & 0x00FF00FFu) + K, o = ((x >> 8) & 0x00FF00FFu) + K;
+    return ((e >> 8) & 0x00800080u) | (o & 0x80008000u);
+}
+
+// keep the bytes of word i of a block (block bytes [4i, 4i+4)) whose block
+// offsets lie in [oa, ob); 0 <= oa < ob <= 64
+CDC_HD uint32_t clip_in_block(uint32_t v, uint32_t i, uint32_t oa, uint32_t ob) {
+    const uint32_t lo = 4 * i;
+    if (lo + 4 <= oa || lo >= ob) return 0;
+    if (lo < oa) v &= 0xFFFFFFFFu << (8 * (oa - lo));
+    if (lo + 4 > ob) v &= 0xFFFFFFFFu >> (8 * (lo + 4 - ob));
+    return v;
+}
+
 // keep the bytes of word `wi` (bytes [4wi, 4wi+4)) that lie in [a, b)
 CDC_HD uint32_t clip_word(uint32_t v, uint64_t wi, uint64_t a, uint64_t b) {
     uint64_t lo = wi << 2;
+    if (lo + 4 <= a || lo >= b) return 0;  // no byte of the word in [a, b)
     if (lo < a) v &= 0xFFFFFFFFu << (8 * (uint32_t)(a - lo));
     if (lo + 4 > b) v &= 0xFFFFFFFFu >> (8 * (uint32_t)(lo + 4 - b));
     return v;
@@ -117,6 +169,30 @@ struct RawView {
 #endif
     }
     CDC_HD uint32_t byte(uint64_t p) const { return (word(p >> 2) >> (8 * (uint32_t)(p & 3))) & 0xFFu; }
+    // the 16-byte granule gi as 4 words
+    CDC_HD void granule(uint64_t gi, uint32_t w[4]) const {
+#if defined(__CUDA_ARCH__)
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(base) + gi);
+        w[0] = v.x ^ inv; w[1] = v.y ^ inv; w[2] = v.z ^ inv; w[3] = v.w ^ inv;
+#else
+        const uint32_t* p = reinterpret_cast<const uint32_t*>(base) + 4 * gi;
+        for (int k = 0; k < 4; k++) w[k] = p[k] ^ inv;
+#endif
+    }
+    // Words of the block holding [a, b) (a < b <= end of that 64-byte block):
+    // the granules that meet [a, b) are loaded (all at once), the others read 0.
+    CDC_HD void block(uint64_t a, uint64_t b, uint32_t w[16]) const {
+        const uint64_t g0 = a >> 4, g1 = (b - 1) >> 4, gb = (a >> 6) << 2;
+        CDC_UNROLL
+        for (int k = 0; k < 4; k++) {
+            const uint64_t g = gb + (uint64_t)k;
+            if (g >= g0 && g <= g1) {
+                granule(g, w + 4 * k);
+            } else {
+                w[4 * k] = w[4 * k + 1] = w[4 * k + 2] = w[4 * k + 3] = 0;
+            }
+        }
+    }
 };
 
 // Per-block summaries: m[b] (block maximum, or for MAXP the offset of the
@@ -138,6 +214,18 @@ struct SumView {
         uint64_t r = b - wb0;
         return (b >= wb0 && r < wn) ? sa[r] : ga[b];
     }
+    // m[] of blocks [16q, 16q + 16) as 4 little-endian words
+    CDC_HD void m16(uint64_t q, uint32_t w[4]) const {
+        const uint64_t b = q << 4, r = b - wb0;
+        const uint8_t* p = (b >= wb0 && r + 16 <= wn) ? sm + r : gm + b;
+#if defined(__CUDA_ARCH__)
+        const uint4 v = *reinterpret_cast<const uint4*>(p);
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+#else
+        const uint32_t* pw = reinterpret_cast<const uint32_t*>(p);
+        for (int k = 0; k < 4; k++) w[k] = pw[k];
+#endif
+    }
     // m[] of blocks [4wi, 4wi + 4) as one little-endian word
     CDC_HD uint32_t m4(uint64_t wi) const {
         uint64_t b = wi << 2, r = b - wb0;
@@ -150,33 +238,17 @@ struct Prm {
     uint32_t w, mn, mx;
 };
 
-// ---- raw helpers (bytes [a, b), a < b) --------------------------------------
+// ---- raw helpers over any span [a, b), a < b (word at a time; the byte rules) --
 
-CDC_HD uint32_t raw_max(const RawView& R, uint64_t a, uint64_t b) {
+CDC_HD uint32_t raw_max_span(const RawView& R, uint64_t a, uint64_t b) {
     uint32_t acc = 0;
     for (uint64_t wi = a >> 2, we = (b + 3) >> 2; wi < we; wi++)
         acc = vmax4(acc, clip_word(R.word(wi), wi, a, b));
     return hmax4(acc);
 }
 
-// maximum of [a, b) and the position of its first occurrence
-CDC_HD void raw_max_first(const RawView& R, uint64_t a, uint64_t b, uint32_t* v, uint64_t* p) {
-    uint32_t M = raw_max(R, a, b);
-    uint32_t Mx = M * 0x01010101u;
-    for (uint64_t wi = a >> 2, we = (b + 3) >> 2; wi < we; wi++) {
-        uint32_t e = clip_word(vcmpeq4(R.word(wi), Mx), wi, a, b);
-        if (e) {
-            *v = M;
-            *p = (wi << 2) + (uint32_t)((ffs32(e) - 1) >> 3);
-            return;
-        }
-    }
-    *v = M;
-    *p = a;  // unreachable: M occurs in [a, b)
-}
-
 // first position in [a, b) whose byte is >= M (M >= 1); b if none
-CDC_HD uint64_t raw_first_geq(const RawView& R, uint64_t a, uint64_t b, uint32_t M, uint32_t* val) {
+CDC_HD uint64_t raw_first_geq_span(const RawView& R, uint64_t a, uint64_t b, uint32_t M, uint32_t* val) {
     uint32_t Mx = M * 0x01010101u;
     for (uint64_t wi = a >> 2, we = (b + 3) >> 2; wi < we; wi++) {
         uint32_t v = R.word(wi);
@@ -190,24 +262,89 @@ CDC_HD uint64_t raw_first_geq(const RawView& R, uint64_t a, uint64_t b, uint32_t
     return b;
 }
 
+// ---- raw helpers inside one 64-byte block (a < b <= end of a's block): the
+// granules are loaded together, then scanned in registers ---------------------
+
+CDC_HD uint32_t raw_max(const RawView& R, uint64_t a, uint64_t b) {
+    uint32_t w[16];
+    R.block(a, b, w);
+    const uint64_t b0 = a & ~63ull;
+    const uint32_t oa = (uint32_t)(a - b0), ob = (uint32_t)(b - b0);
+    ByteMax m;
+    CDC_UNROLL
+    for (uint32_t i = 0; i < 16; i++) m.add(clip_in_block(w[i], i, oa, ob));
+    return m.get();
+}
+
+// first position in [a, b) whose byte is >= M (M >= 1); b if none
+CDC_HD uint64_t raw_first_geq(const RawView& R, uint64_t a, uint64_t b, uint32_t M, uint32_t* val) {
+    uint32_t w[16];
+    R.block(a, b, w);
+    const uint64_t b0 = a & ~63ull;
+    const uint32_t oa = (uint32_t)(a - b0), ob = (uint32_t)(b - b0), K = ge_key(M);
+    CDC_UNROLL
+    for (uint32_t i = 0; i < 16; i++) {
+        const uint32_t f = ge_flags(clip_in_block(w[i], i, oa, ob), K);
+        if (f) {
+            const uint32_t k = (uint32_t)((ffs32(f) - 1) >> 3);
+            *val = (w[i] >> (8 * k)) & 0xFFu;
+            return b0 + 4 * i + k;
+        }
+    }
+    return b;
+}
+
+// maximum of [a, b) and the position of its first occurrence (one block)
+CDC_HD void raw_max_first(const RawView& R, uint64_t a, uint64_t b, uint32_t* v, uint64_t* p) {
+    uint32_t w[16];
+    R.block(a, b, w);
+    const uint64_t b0 = a & ~63ull;
+    const uint32_t oa = (uint32_t)(a - b0), ob = (uint32_t)(b - b0);
+    ByteMax m;
+    CDC_UNROLL
+    for (uint32_t i = 0; i < 16; i++) m.add(clip_in_block(w[i], i, oa, ob));
+    const uint32_t M = m.get();
+    *v = M;
+    *p = a;
+    if (M == 0) return;  // every byte is 0: the first is at a
+    const uint32_t K = ge_key(M);
+    CDC_UNROLL
+    for (uint32_t i = 0; i < 16; i++) {
+        const uint32_t f = ge_flags(clip_in_block(w[i], i, oa, ob), K);
+        if (f) {
+            *p = b0 + 4 * i + (uint32_t)((ffs32(f) - 1) >> 3);
+            return;
+        }
+    }
+}
+
 // ---- summary helpers --------------------------------------------------------
 
-// maximum of m[] over blocks [b0, b1), b0 < b1
+// maximum of m[] over blocks [b0, b1), b0 < b1 (16 blocks per step)
 CDC_HD uint32_t sum_max(const SumView& S, uint64_t b0, uint64_t b1) {
-    uint32_t acc = 0;
-    for (uint64_t wi = b0 >> 2, we = (b1 + 3) >> 2; wi < we; wi++) {
-        acc = vmax4(acc, clip_word(S.m4(wi), wi, b0, b1));
-        if (vcmpeq4(acc, 0xFFFFFFFFu)) return 255;  // cannot grow further
+    ByteMax m;
+    for (uint64_t q = b0 >> 4, qe = (b1 + 15) >> 4; q < qe; q++) {
+        uint32_t w[4];
+        S.m16(q, w);
+        CDC_UNROLL
+        for (int k = 0; k < 4; k++) m.add(clip_word(w[k], 4 * q + (uint64_t)k, b0, b1));
+        if (m.full()) return 255;  // cannot grow further
     }
-    return hmax4(acc);
+    return m.get();
 }
 
 // first block in [b0, b1) with m[] >= M (M >= 1); b1 if none
 CDC_HD uint64_t sum_first_geq(const SumView& S, uint64_t b0, uint64_t b1, uint32_t M) {
-    uint32_t Mx = M * 0x01010101u;
-    for (uint64_t wi = b0 >> 2, we = (b1 + 3) >> 2; wi < we; wi++) {
-        uint32_t h = clip_word(vcmpge4(S.m4(wi), Mx), wi, b0, b1);
-        if (h) return (wi << 2) + (uint32_t)((ffs32(h) - 1) >> 3);
+    const uint32_t K = ge_key(M);
+    for (uint64_t q = b0 >> 4, qe = (b1 + 15) >> 4; q < qe; q++) {
+        uint32_t w[4];
+        S.m16(q, w);
+        CDC_UNROLL
+        for (int k = 0; k < 4; k++) {
+            const uint64_t wi = 4 * q + (uint64_t)k;
+            const uint32_t f = ge_flags(clip_word(w[k], wi, b0, b1), K);
+            if (f) return (wi << 2) + (uint32_t)((ffs32(f) - 1) >> 3);
+        }
     }
     return b1;
 }
@@ -385,12 +522,12 @@ CDC_HD uint64_t next_ram_bytes(const RawView& R, const Prm& P, uint64_t fhi, uin
     if (fhi - s <= P.w) return fhi;
     uint64_t limit = umin64(fhi, s + P.mx);
     uint64_t t = s + P.w;
-    uint32_t M = raw_max(R, s, t);
+    uint32_t M = raw_max_span(R, s, t);
     uint64_t j0 = umax64(t, s + P.mn - 1);
     if (j0 >= limit) return limit;
     if (M == 0) return j0 + 1;
     uint32_t val;
-    uint64_t j = raw_first_geq(R, j0, limit, M, &val);
+    uint64_t j = raw_first_geq_span(R, j0, limit, M, &val);
     return j < limit ? j + 1 : limit;
 }
 
@@ -404,7 +541,7 @@ CDC_HD uint64_t next_ae_bytes(const RawView& R, const Prm& P, uint64_t fhi, uint
         if (t >= limit) return limit;
         if (v == 255) return t + 1;
         uint32_t val;
-        uint64_t q = raw_first_geq(R, cur, t + 1, v + 1, &val);
+        uint64_t q = raw_first_geq_span(R, cur, t + 1, v + 1, &val);
         if (q > t) return t + 1;
         p = q; v = val; cur = q + 1;
     }
@@ -413,9 +550,9 @@ CDC_HD uint64_t next_ae_bytes(const RawView& R, const Prm& P, uint64_t fhi, uint
 CDC_HD bool maxp_target_bytes(const RawView& R, uint64_t c, uint32_t w) {
     uint32_t v = R.byte(c);
     if (v == 0) return false;
-    uint32_t lm = raw_max(R, c - w, c);
+    uint32_t lm = raw_max_span(R, c - w, c);
     if (lm >= v) return false;
-    return raw_max(R, c + 1, c + 1 + w) < v;
+    return raw_max_span(R, c + 1, c + 1 + w) < v;
 }
 
 CDC_HD uint64_t next_maxp_bytes(const RawView& R, const Prm& P, uint64_t flo, uint64_t fhi,
