@@ -261,8 +261,12 @@ static uint64_t pick_span(cdc_handle h, cdc_params p, uint64_t seg) {
     return sp;
 }
 
+// summary blocks staged per segment: the segment, the room its bounds may
+// move out of quiet regions (up to about twice max, see the adj_* fields),
+// and max beyond its end, where its chains' last steps read
 static uint32_t pick_win(cdc_params p, uint64_t seg) {
-    uint64_t blocks = (seg + (uint64_t)p.max + 2 * 64) / 64 + 32;
+    const uint64_t mx4k = ((uint64_t)p.max + 4095) & ~4095ull;
+    uint64_t blocks = (seg + 2 * mx4k + (uint64_t)p.max + 2 * 64) / 64 + 32;
     blocks = (blocks + 15) & ~15ull;
     const uint64_t cap = 24u << 10;  // bytes of shared memory per summary array
     if (blocks > cap) blocks = cap;
