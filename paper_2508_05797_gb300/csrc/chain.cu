@@ -31,7 +31,7 @@
 // Every wait (a segment on its predecessor's speculation) is bounded.
 #include "cdc_device.cuh"
 #include "cdc_launch.h"
-#include "warp_rules.cuh"
+#include "warp_fast.cuh"
 
 namespace cdc {
 
@@ -278,6 +278,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
             S.wb0 = wb0;
             S.wn = wn;
         }
+        const Win W{dsm, dsm + A.win, S.wb0 << 6, (uint32_t)(S.wn << 6)};
         __syncthreads();
 
         auto lap = [&](int k) {
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                     uint32_t k;
                     uint64_t dd;
                     const long long c1 = A.stats ? clock64() : 0;
-                    v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+                    v = f_advance<RULE>(W, S, R, P, flo, fhi, v, seg_hi, &k, &dd);
                     cc += k;
                     if (lane == 0) stat_add(A, STAT_WARP_STEPS, 1);
                     if (A.stats && lane == 0) stat_add(A, STAT_CYC_WSTEP, (unsigned long long)(clock64() - c1));
