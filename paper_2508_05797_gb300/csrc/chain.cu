@@ -1003,6 +1003,7 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
             S.wn = wn;
             __syncwarp();
         }
+        const Win W{dsm, dsm + A.win, S.wb0 << 6, (uint32_t)(S.wn << 6)};
         uint64_t v = first ? flo : st->entry_pos;
         uint64_t kb = excl, held = 0;
         uint32_t nb = 0;
@@ -1019,7 +1020,7 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
             while (v < seg_hi) {
                 uint32_t k;
                 uint64_t dd;
-                const uint64_t e = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+                const uint64_t e = f_advance<RULE>(W, S, R, P, flo, fhi, v, seg_hi, &k, &dd);
                 if (lane == 0) stat_add(A, STAT_OUT_STEPS, 1);
                 for (uint32_t i = 0; i < k; i++) {
                     const uint64_t p = v + i * dd;
