@@ -73,20 +73,6 @@ __device__ __forceinline__ uint32_t block_key(const uint8_t* blk, uint32_t sw, u
     return max(acc & 0xFFFFu, acc >> 16);
 }
 
-// Any byte at offsets [o0, o1] (inclusive) of a 64-byte block >= v (1 <= v <= 255):
-// bytes in 16-bit lanes, lane + (0x8000 - v) reaches bit 15 exactly when byte >= v.
-__device__ __forceinline__ bool block_any_geq(const uint8_t* blk, uint32_t o0, uint32_t o1, uint32_t v) {
-    const uint32_t K = (0x8000u - v) * 0x00010001u;
-    for (uint32_t q = o0 >> 2; q <= (o1 >> 2); q++) {
-        uint32_t x = *reinterpret_cast<const uint32_t*>(blk + 4 * q);
-        if (4 * q < o0) x &= 0xFFFFFFFFu << (8 * (o0 - 4 * q));
-        if (4 * q + 3 > o1) x &= 0xFFFFFFFFu >> (8 * (4 * q + 3 - o1));
-        const uint32_t e = __byte_perm(x, 0, 0x4240), o = __byte_perm(x, 0, 0x4341);
-        if (((e + K) | (o + K)) & 0x80008000u) return true;
-    }
-    return false;
-}
-
 // issue the copy of bytes [r0, r1) (physical positions) into the stage buffer
 // `dst`, whose first byte stands for position r0; clipped to [glo, ghi).
 __device__ __forceinline__ void issue_tile(const uint8_t* base, uint64_t glo, uint64_t ghi, uint64_t r0,
@@ -188,6 +174,9 @@ __global__ void __launch_bounds__(MP_THREADS, 4) k_summary_maxp(SumLaunch a) {
     uint8_t* bl = bf + nb;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + ((2 * sbytes + 3 * nb + 15) & ~15u));
     __shared__ unsigned int supcnt[MP_TILE_BLOCKS / 64];
+    __shared__ uint16_t qlist[MP_TILE_BLOCKS];  // candidates waiting for a byte test of their end blocks
+    __shared__ uint8_t qres[MP_TILE_BLOCKS];
+    __shared__ unsigned int qn;
     if (blockIdx.x == 0 && tid == 0) reset_ctrl(a.ctrl);
     const uint64_t ntiles = (a.nblk + MP_TILE_BLOCKS - 1) / MP_TILE_BLOCKS;
     if (tid == 0) {
@@ -196,6 +185,7 @@ __global__ void __launch_bounds__(MP_THREADS, 4) k_summary_maxp(SumLaunch a) {
         fence_mbar_init();
     }
     if (tid < MP_TILE_BLOCKS / 64) supcnt[tid] = 0;
+    if (tid == 0) qn = 0;
     __syncthreads();
     const uint64_t g = gridDim.x;
     // stage block 0 stands for global block t * MP_TILE_BLOCKS - hb (negative
@@ -249,30 +239,75 @@ __global__ void __launch_bounds__(MP_THREADS, 4) k_summary_maxp(SumLaunch a) {
             bl[sb] = (uint8_t)(kl & 0xFFu);
         }
         __syncthreads();
-        // 2) target test, one thread per tile block
-        for (uint32_t lb = tid; lb < MP_TILE_BLOCKS; lb += MP_THREADS) {  // one block per thread
+        // 2) target test, one thread per tile block. Interior blocks of the
+        // window are judged by their maxima; a candidate whose partial end
+        // blocks may hold a byte >= its value is queued, and whole warps test
+        // those bytes (16 lanes per end block).
+        static_assert(MP_TILE_BLOCKS == MP_THREADS, "one tile block per thread");
+        uint32_t state = 0;  // 0: no target, 1: target, 2: queued
+        {
+            const uint32_t lb = (uint32_t)tid;
             const uint64_t gb = t * MP_TILE_BLOCKS + lb;
             const uint32_t sbi = hb + lb;  // stage index of this block
             const uint32_t v = bm[sbi];
             const uint64_t p = gb * 64 + bf[sbi];
-            bool ok = gb < a.nblk && v != 0 && bf[sbi] == bl[sbi] && p >= a.lo + w && p + w < a.hi;
-            if (ok) {
+            if (gb < a.nblk && v != 0 && bf[sbi] == bl[sbi] && p >= a.lo + w && p + w < a.hi) {
                 const uint64_t wl = p - w, wr = p + w;  // window [wl, wr]
-                const uint64_t kb0 = wl >> 6, kb1 = wr >> 6;
-                for (uint64_t kb = kb0; kb <= kb1 && ok; kb++) {
-                    if (kb == gb) continue;
-                    const uint32_t si = (uint32_t)((int64_t)kb - sb0);
-                    if (bm[si] < v) continue;
-                    const uint64_t blo = kb * 64, bhi = blo + 63;
-                    if (blo >= wl && bhi <= wr) { ok = false; break; }
-                    const uint64_t x0 = blo > wl ? blo : wl, x1 = bhi < wr ? bhi : wr;
-                    if (block_any_geq(tb + (size_t)si * 64, (uint32_t)(x0 - blo), (uint32_t)(x1 - blo), v)) ok = false;
+                const uint32_t s0 = (uint32_t)((int64_t)(wl >> 6) - sb0), s1 = (uint32_t)((int64_t)(wr >> 6) - sb0);
+                bool ok = true;
+                for (uint32_t si = s0 + 1; si < s1 && ok; si++)
+                    if (si != sbi && bm[si] >= v) ok = false;
+                bool queue = false;
+                if (ok && s0 != sbi && bm[s0] >= v) {
+                    if ((wl & 63) == 0) ok = false;  // the whole block lies in the window
+                    else queue = true;
                 }
+                if (ok && s1 != sbi && s1 != s0 && bm[s1] >= v) {
+                    if ((wr & 63) == 63) ok = false;
+                    else queue = true;
+                }
+                state = ok ? (queue ? 2u : 1u) : 0u;
             }
-            if (gb < a.nblk) a.smax[gb] = ok ? bf[sbi] : (uint8_t)0xFFu;
-            // targets per 4 KiB superblock (64 blocks = 2 warps of this loop)
+            if (state == 2) qlist[atomicAdd(&qn, 1u)] = (uint16_t)lb;
+        }
+        __syncthreads();
+        for (uint32_t q = (uint32_t)(tid >> 5); q < qn; q += MP_THREADS / 32) {
+            const int lane = tid & 31;
+            const uint32_t lb = qlist[q];
+            const uint64_t gb = t * MP_TILE_BLOCKS + lb;
+            const uint32_t sbi = hb + lb;
+            const uint32_t v = bm[sbi];
+            const uint64_t p = gb * 64 + bf[sbi], wl = p - w, wr = p + w;
+            const uint32_t s0 = (uint32_t)((int64_t)(wl >> 6) - sb0), s1 = (uint32_t)((int64_t)(wr >> 6) - sb0);
+            // lanes 0..15: words of the left end block from wl on; 16..31: right end block up to wr
+            const bool left = lane < 16;
+            const uint32_t si = left ? s0 : s1;
+            const bool need = si != sbi && (left || s1 != s0) && bm[si] >= v;
+            uint32_t f = 0;
+            if (need) {
+                const uint32_t j = (uint32_t)(lane & 15);
+                const uint32_t o0 = left ? (uint32_t)(wl & 63) : 0u, o1 = left ? 63u : (uint32_t)(wr & 63);
+                uint32_t x = *reinterpret_cast<const uint32_t*>(tb + (size_t)si * 64 + 4 * j);
+                if (4 * j + 3 < o0 || 4 * j > o1) x = 0;
+                if (4 * j < o0 && 4 * j + 3 >= o0) x &= 0xFFFFFFFFu << (8 * (o0 - 4 * j));
+                if (4 * j <= o1 && 4 * j + 3 > o1) x &= 0xFFFFFFFFu >> (8 * (4 * j + 3 - o1));
+                const uint32_t K = (0x8000u - v) * 0x00010001u;
+                const uint32_t e = __byte_perm(x, 0, 0x4240), o = __byte_perm(x, 0, 0x4341);
+                f = ((e + K) | (o + K)) & 0x80008000u;
+            }
+            const uint32_t bal = __ballot_sync(FULL, f != 0);
+            if (lane == 0) qres[lb] = bal == 0 ? 1 : 0;
+        }
+        __syncthreads();
+        {
+            const uint32_t lb = (uint32_t)tid;
+            const uint64_t gb = t * MP_TILE_BLOCKS + lb;
+            const bool ok = state == 1 || (state == 2 && qres[lb]);
+            if (gb < a.nblk) a.smax[gb] = ok ? bf[hb + lb] : (uint8_t)0xFFu;
+            // targets per 4 KiB superblock (64 blocks = 2 warps)
             const uint32_t cntw = __popc(__ballot_sync(FULL, ok));
             if ((tid & 31) == 0 && cntw) atomicAdd(&supcnt[lb >> 6], cntw);
+            if (tid == 0) qn = 0;
         }
         __syncthreads();
         if (tid < MP_TILE_BLOCKS / 64) {
