@@ -196,6 +196,97 @@ def cpu_baseline(sample_bytes: int = 256 * MIB):
                 sample_bytes // MIB), "seconds": round(dt, 2)}
 
 
+def batched_workload(dev, n_files: int = 100_000, warmup: int = 2, reps: int = 3):
+    """The batched form against a per-file launch loop: files with log-normal
+    sizes (median 64 KiB, sigma 1.5, clipped to 1 B .. 256 MiB, seed 3) of
+    mixed content packed in one device arena, chunked with MAXP and RAM at
+    8 KiB mean. The batched call is autotuned (cdc_autotune), captured in a
+    CUDA graph and replayed; the loop calls cdc_chunk_async once per file.
+    Both outputs are compared bit for bit."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2508_05797_gb300 import Chunker
+    from paper_2508_05797_gb300.cdc import Params, alg_id
+
+    sizes = synth.lognormal_sizes(3, n_files, 65536, 1.5, 1, 256 * MIB).astype(np.int64)
+    off = np.zeros(n_files + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    total = int(off[-1])
+    host = torch.empty(total, dtype=torch.uint8, pin_memory=True)
+    synth.mixed(3, total, out=host.numpy())
+    arena = host.to(dev)
+    del host
+    d_off = torch.from_numpy(off).to(dev)
+    t = wtable()["mixed_4g_seed1"]
+    res = {"workload": "%d files, log-normal sizes (median 64 KiB, sigma 1.5, 1 B..256 MiB, seed 3), mixed content, "
+                       "%.2f GB in one device arena; 8 KiB mean" % (n_files, total / 1e9),
+           "bytes": total}
+    stream = torch.cuda.Stream(dev)
+    for alg in ("maxp", "ram"):
+        e = t[alg]["8192"]
+        w, mn, mx = e["w"], e["min"], e["max"]
+        ck = Chunker(dev.index)
+        cap = total // mn + n_files + 1
+        out = torch.empty(cap, dtype=torch.int64, device=dev)
+        idx = torch.empty(n_files + 1, dtype=torch.int64, device=dev)
+        seg, wc, tune_ms = ck.autotune(arena, alg, w, mn, mx, out=out, file_off=d_off, index=idx, stream=stream)
+        ck.reserve(alg, w, mn, mx, total, n_files)
+        with torch.cuda.stream(stream):
+            ck.chunk_batch(arena, d_off, alg, w, mn, mx, out=out, index=idx, stream=stream, sync=False)
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            ck.chunk_batch(arena, d_off, alg, w, mn, mx, out=out, index=idx, stream=stream, sync=False)
+        for _ in range(warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ck.sync_status(stream)
+        batch_ms = e0.elapsed_time(e1) / reps
+        index = idx.cpu().numpy()
+        # per-file loop through the single-stream entry point
+        out2 = torch.full((cap,), -1, dtype=torch.int64, device=dev)
+        cnt = torch.zeros(n_files, dtype=torch.int64, device=dev)
+        lib, h, prm, a = ck.lib, ck.h, Params(w, mn, mx), alg_id(alg)
+        base, obase, cbase = arena.data_ptr(), out2.data_ptr(), cnt.data_ptr()
+        sh = stream.cuda_stream
+        fn = lib.cdc_chunk_async
+        torch.cuda.synchronize()
+        e0.record(stream)
+        t0 = time.perf_counter()
+        for f in range(n_files):
+            st = fn(h, a, prm, base + int(off[f]), int(sizes[f]), obase + 8 * int(index[f]),
+                    int(index[f + 1] - index[f]), cbase + 8 * f, sh)
+            if st:
+                raise RuntimeError("cdc_chunk_async failed on file %d: status %d" % (f, st))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        loop_wall = time.perf_counter() - t0
+        loop_ms = e0.elapsed_time(e1)
+        ck.sync_status(stream)
+        same = bool(torch.equal(out2[:int(index[-1])], out[:int(index[-1])]) and
+                    torch.equal(cnt, torch.from_numpy(np.diff(index)).to(dev)))
+        res[alg] = {"batched_GBps": round(total / (batch_ms / 1e3) / 1e9, 1), "batched_ms": round(batch_ms, 3),
+                    "loop_GBps": round(total / (loop_ms / 1e3) / 1e9, 2), "loop_ms": round(loop_ms, 1),
+                    "loop_host_s": round(loop_wall, 2), "speedup": round(loop_ms / batch_ms, 1),
+                    "bit_exact": same, "autotuned": {"segment": seg, "warp_chains": wc, "ms": round(tune_ms, 3)},
+                    "boundaries": int(index[-1])}
+        ck.close()
+        del out, out2, idx, cnt, g
+    del arena
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -236,6 +327,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--batched-files", type=int, default=100_000)
     ap.add_argument("--algs", default=",".join(ALGS), help="subset of ram,ae,maxp (profiling cases)")
     ap.add_argument("--means", default=",".join(map(str, MEANS)), help="subset of 4096,8192,16384")
     ap.add_argument("--len-mib", type=int, default=STREAM_LEN // MIB,
@@ -361,6 +454,13 @@ def main():
         line["e2e"] = {"value": round(ncfg * n * e2e_steps * world / dt / 1e9, 2), "unit": "GB/s",
                        "h2d_bytes_per_step": ncfg * n, "d2h_bytes_per_step": int(d2h),
                        "steps": e2e_steps}
+    if rank == 0 and not args.no_batched:
+        for ck in handles:
+            ck.close()
+        handles = []
+        del data
+        torch.cuda.empty_cache()
+        line["batched"] = batched_workload(dev, n_files=args.batched_files)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

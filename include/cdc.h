@@ -166,6 +166,22 @@ typedef enum {
 CDC_API cdc_status cdc_set_option(cdc_handle h, cdc_option opt, int64_t value);
 CDC_API cdc_status cdc_get_option(cdc_handle h, cdc_option opt, int64_t* value);
 
+/* Autotuner for the segment size and the warp-chain threshold: runs the
+ * chunk path on the caller's input for each pair of a small grid (segment
+ * bytes: automatic, 128 KiB, 256 KiB, 512 KiB, 1 MiB; warp chains: 32, 64, 96),
+ * twice each, timed with CUDA events on `stream`, and keeps the fastest pair on
+ * the handle (CDC_OPT_SEGMENT, CDC_OPT_WARP_CHAINS), reported in *seg_out,
+ * *warp_chains_out and *best_ms (each may be NULL). Every setting gives the
+ * same boundaries, so tuning never changes results. d_file_off / n_files /
+ * d_bounds_index as for cdc_chunk_batch (d_file_off NULL: one stream of len
+ * bytes); d_bounds (capacity entries) is overwritten. Not during stream
+ * capture (CDC_ERR_INVALID); synchronises `stream`. On an error the options
+ * are left as they were. The paper has no counterpart. */
+CDC_API cdc_status cdc_autotune(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
+                                const uint64_t* d_file_off, size_t n_files, uint64_t* d_bounds,
+                                uint64_t* d_bounds_index, size_t capacity, int64_t* seg_out,
+                                int64_t* warp_chains_out, float* best_ms, cdc_stream stream);
+
 /* Device time in milliseconds of the two stages of the last call on the
  * handle (block summaries; chain), measured with CUDA events on the call's
  * stream. Synchronises on those events. Either pointer may be NULL. */
@@ -185,8 +201,10 @@ CDC_API cdc_status cdc_profile_collect(cdc_handle h, int* calls, double* summary
  * entries, segments whose position hash filled, fallback walks in the
  * resolution, output steps, empty segments, chains handed to whole warps,
  * then clock cycles summed over segments (set-up, speculation, merge
- * resolution, stitching), per-thread rounds, and the cycles of the rounds and
- * of the one-warp-per-chain phase (19 counters in all).
+ * resolution, stitching), per-thread rounds, the cycles of the rounds and of
+ * the one-warp-per-chain phase, the cycles inside that phase's chain steps and
+ * hash inserts, the hash slots those inserts probed, stitch walks of more than
+ * 64 steps, and (steps << 32 | segment) of the longest one (24 counters).
  * Synchronises `stream`. */
 CDC_API cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream stream);
 
@@ -227,7 +245,7 @@ CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
  *     wrong results. Serialise them.
  */
 #define CDC_STATIC_MAX_LEN ((size_t)16 << 20)
-#define CDC_STATIC_SCRATCH_BYTES ((size_t)10785280)
+#define CDC_STATIC_SCRATCH_BYTES ((size_t)10785536)
 
 CDC_API cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
                                     uint64_t* out_bounds, size_t* n, cdc_stream stream);

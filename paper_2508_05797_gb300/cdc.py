@@ -19,7 +19,7 @@ OPT_STATS = 6
 OPT_WARP_CHAINS = 7
 STAT_NAMES = ["segments", "thread_steps", "warp_steps", "merges", "stitch_walks", "stitch_steps", "unknown",
               "hash_full", "scan_follows", "out_steps", "empty", "survivors", "cyc_setup", "cyc_threads",
-              "cyc_warps", "cyc_stitch", "rounds", "cyc_rounds", "cyc_surv", "cyc_wstep", "cyc_whash", "probes"]
+              "cyc_warps", "cyc_stitch", "rounds", "cyc_rounds", "cyc_surv", "cyc_wstep", "cyc_whash", "probes", "stitch_long", "stitch_maxw"]
 STATUS = ["CDC_OK", "CDC_ERR_INVALID", "CDC_ERR_CAPACITY", "CDC_ERR_CUDA", "CDC_ERR_TIMEOUT",
           "CDC_ERR_NOMEM", "CDC_ERR_INTERNAL"]
 OK, ERR_INVALID, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_INTERNAL = range(7)
@@ -74,6 +74,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
                                      ctypes.POINTER(i64)], i32),
             "cdc_stats": ([vp, vp, i32, vp], i32),
             "cdc_chunk_static": ([i32, P, vp, sz, vp, ctypes.POINTER(sz), vp], i32),
+            "cdc_autotune": ([vp, i32, P, vp, sz, vp, sz, vp, vp, sz, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                              ctypes.POINTER(ctypes.c_float), vp], i32),
             "cdc_status_string": ([i32], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -87,7 +89,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return ["cdc_create", "cdc_destroy", "cdc_chunk", "cdc_chunk_async", "cdc_chunk_batch", "cdc_chunk_host",
             "cdc_reserve", "cdc_sync_status", "cdc_set_option", "cdc_get_option", "cdc_last_timing",
-            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_status_string"]
+            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_status_string"]
 
 
 def alg_id(alg) -> int:
@@ -219,6 +221,26 @@ class Chunker:
                                      out.ctypes.data, ctypes.byref(cap), _stream_handle(stream))
         _check(st, "cdc_chunk_host (count %d)" % cap.value)
         return out[:cap.value]
+
+    def autotune(self, data, alg, w: int, mn: int, mx: int, out=None, file_off=None, index=None, stream=None):
+        """cdc_autotune on a uint8 CUDA tensor (one stream, or a packed arena
+        with file_off). Returns (segment bytes, warp chains, best ms); the
+        handle keeps the chosen options."""
+        import torch
+        assert data.dtype == torch.uint8 and data.is_cuda
+        n = data.numel()
+        n_files = 0 if file_off is None else file_off.numel() - 1
+        if out is None:
+            out = torch.empty(n // max(mn, 1) + n_files + 1, dtype=torch.int64, device=data.device)
+        if file_off is not None and index is None:
+            index = torch.empty(n_files + 1, dtype=torch.int64, device=data.device)
+        sg, wc, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_float()
+        st = self.lib.cdc_autotune(self.h, alg_id(alg), Params(w, mn, mx), data.data_ptr(), n,
+                                   file_off.data_ptr() if file_off is not None else None, n_files, out.data_ptr(),
+                                   index.data_ptr() if index is not None else None, out.numel(), ctypes.byref(sg),
+                                   ctypes.byref(wc), ctypes.byref(ms), _stream_handle(stream))
+        _check(st, "cdc_autotune")
+        return sg.value, wc.value, ms.value
 
     def reserve(self, alg, w: int, mn: int, mx: int, n: int, n_files: int = 0):
         _check(self.lib.cdc_reserve(self.h, alg_id(alg), Params(w, mn, mx), n, n_files), "cdc_reserve")

@@ -521,6 +521,77 @@ extern "C" cdc_status cdc_chunk_host(cdc_handle h, cdc_alg alg, cdc_params p, co
     return CDC_OK;
 }
 
+// ---- autotuner -------------------------------------------------------------------
+//
+// Times the chunk path on the caller's input for each (segment size,
+// warp-chain threshold) pair of a small grid, twice each (CUDA events around
+// the stages on `stream`), and keeps the fastest pair on the handle. Every
+// setting gives identical boundaries; only the time differs.
+extern "C" cdc_status cdc_autotune(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
+                                   const uint64_t* d_file_off, size_t n_files, uint64_t* d_bounds,
+                                   uint64_t* d_bounds_index, size_t capacity, int64_t* seg_out,
+                                   int64_t* warp_chains_out, float* best_ms, cdc_stream stream) {
+    if (!h || !valid_params(alg, p) || !data || !d_bounds || len == 0) return CDC_ERR_INVALID;
+    const bool batch = d_file_off != nullptr;
+    if (batch && (!d_bounds_index || n_files == 0 || n_files > 0xFFFFFFFFull)) return CDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (capturing(st)) return CDC_ERR_INVALID;
+    cudaSetDevice(h->device);
+    static const int64_t kSeg[] = {0, 128 << 10, 256 << 10, 512 << 10, 1 << 20};
+    static const int64_t kWarp[] = {32, 64, 96};
+    const int64_t seg0 = h->seg, wc0 = h->warp_chains, prof0 = h->profile;
+    h->profile = 0;
+    float best = -1.0f;
+    int64_t best_seg = seg0, best_wc = wc0;
+    cdc_status err = CDC_OK;
+    for (int64_t sg : kSeg) {
+        for (int64_t wc : kWarp) {
+            h->seg = sg;
+            h->warp_chains = wc;
+            float t = -1.0f;
+            for (int rep = 0; rep < 2 && err == CDC_OK; rep++) {
+                if (batch && cudaMemsetAsync(d_bounds_index, 0, (n_files + 1) * sizeof(uint64_t), st) != cudaSuccess) {
+                    err = CDC_ERR_CUDA;
+                    break;
+                }
+                cdc_status s = run(h, alg, p, data, len, d_file_off, batch ? n_files : 0, d_bounds, capacity,
+                                   batch ? d_bounds_index : nullptr, nullptr, st);
+                uint64_t total = 0;
+                if (s == CDC_OK) s = collect(h, st, &total);
+                if (s == CDC_OK && total > capacity) s = CDC_ERR_CAPACITY;
+                if (s != CDC_OK) {
+                    err = s;
+                    break;
+                }
+                float a = 0, b = 0;
+                cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+                cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
+                if (t < 0 || a + b < t) t = a + b;
+            }
+            if (err != CDC_OK) break;
+            if (best < 0 || t < best) {
+                best = t;
+                best_seg = sg;
+                best_wc = wc;
+            }
+        }
+        if (err != CDC_OK) break;
+    }
+    h->profile = prof0;
+    h->timed = false;
+    if (err != CDC_OK) {
+        h->seg = seg0;
+        h->warp_chains = wc0;
+        return err;
+    }
+    h->seg = best_seg;
+    h->warp_chains = best_wc;
+    if (seg_out) *seg_out = best_seg;
+    if (warp_chains_out) *warp_chains_out = best_wc;
+    if (best_ms) *best_ms = best;
+    return CDC_OK;
+}
+
 extern "C" cdc_status cdc_reserve(cdc_handle h, cdc_alg alg, cdc_params p, size_t len, size_t n_files) {
     if (!h || !valid_params(alg, p)) return CDC_ERR_INVALID;
     cudaSetDevice(h->device);
@@ -627,7 +698,7 @@ constexpr uint64_t kFixSegSlot = 3584;    // >= sizeof(SegState), checked at set
 constexpr uint64_t kFixGroupSlot = 2048;  // >= sizeof(GroupState), checked at set-up
 constexpr uint64_t kFixHashSlot = 16384;  // >= a segment's position hash, checked at set-up
 constexpr uint64_t kFixGroups = kFixItems / GS + 2;
-constexpr uint64_t kFixCtrlBytes = 256;
+constexpr uint64_t kFixCtrlBytes = 512;
 constexpr uint64_t kFixOffSmax = kFixCtrlBytes;
 constexpr uint64_t kFixOffSarg = kFixOffSmax + kFixSumBytes;
 constexpr uint64_t kFixOffSup = kFixOffSarg + kFixSumBytes;

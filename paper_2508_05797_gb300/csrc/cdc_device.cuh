@@ -20,7 +20,7 @@ struct Ctrl {
     unsigned int err;            // sticky error bits, cleared by the host
     unsigned int stats_on;       // 1: kernels accumulate the counters below
     unsigned int pad[5];
-    unsigned long long stats[22];  // see STAT_* (reset by the host)
+    unsigned long long stats[24];  // see STAT_* (reset by the host)
 };
 enum : int {
     STAT_SEGMENTS = 0,      // non-empty segments speculated
@@ -45,7 +45,9 @@ enum : int {
     STAT_CYC_WSTEP = 19,    // cycles inside whole-warp chain steps of that phase (summed over steps)
     STAT_CYC_WHASH = 20,    // cycles of their position-hash inserts
     STAT_PROBES = 21,       // hash slots probed by those inserts
-    STAT_N = 22
+    STAT_STITCH_LONG = 22,  // stitch walks of more than 64 steps
+    STAT_STITCH_MAXW = 23,  // (steps << 32) | segment of the longest stitch walk
+    STAT_N = 24
 };
 enum : unsigned int { ERR_TIMEOUT = 1u, ERR_INTERNAL = 2u };
 

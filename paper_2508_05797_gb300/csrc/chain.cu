@@ -500,8 +500,9 @@ template <int RULE>
 __device__ uint32_t stitch_walk(const ChainLaunch& A, const SumView& S, const RawView& R, const Prm& P,
                                 const unsigned long long* ht, const unsigned long long* X, const unsigned int* cnt,
                                 uint64_t seg_lo, uint64_t seg_hi, uint64_t flo, uint64_t fhi, bool last, uint64_t e,
-                                uint64_t* ux) {
+                                uint64_t* ux, uint64_t item) {
     const int lane = threadIdx.x & 31;
+    uint32_t nsteps = 0;
     uint64_t v = e;
     uint32_t ne = 0, res = STAB_UNKNOWN;
     while (v < seg_hi) {
@@ -515,6 +516,7 @@ __device__ uint32_t stitch_walk(const ChainLaunch& A, const SumView& S, const Ra
         uint64_t dd;
         v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
         ne += k;
+        nsteps++;
         if (lane == 0) stat_add(A, STAT_STITCH_STEPS, 1);
     }
     *ux = 0;
@@ -533,6 +535,10 @@ __device__ uint32_t stitch_walk(const ChainLaunch& A, const SumView& S, const Ra
     if (lane == 0) {
         stat_add(A, STAT_STITCH_WALKS, 1);
         if (res & STAB_UNKNOWN) stat_add(A, STAT_UNKNOWN, 1);
+        if (A.stats && nsteps > 64) {
+            stat_add(A, STAT_STITCH_LONG, 1);
+            atomicMax(&A.ctrl->stats[STAT_STITCH_MAXW], ((unsigned long long)nsteps << 32) | (item & 0xFFFFFFFFull));
+        }
     }
     return res;
 }
@@ -580,7 +586,7 @@ __global__ void __launch_bounds__(NL) k_stitch(ChainLaunch A) {
         const uint32_t geo = me->geo;
         const bool first = geo & GEO_FIRST, last = geo & GEO_LAST, empty = geo & GEO_EMPTY;
         uint32_t tab;
-        unsigned long long unk = 0;
+        unsigned long long unk = ~0ull;  // no position: slots of chains that never ran stay so
         if (first) {
             tab = stab_enc(0, me->cnt[0] - 1 + (last ? 1u : 0u)) | STAB_CONST;
         } else if (empty) {
@@ -600,7 +606,7 @@ __global__ void __launch_bounds__(NL) k_stitch(ChainLaunch A) {
                 const uint32_t same = __ballot_sync(FULL, xp == e) & todo;
                 uint64_t ux;
                 const uint32_t res = stitch_walk<RULE>(A, S, R, P, sh.ht, sh.X, sh.cnt, seg_lo, seg_hi, flo, fhi,
-                                                       last, e, &ux);
+                                                       last, e, &ux, item);
                 if ((same >> lane) & 1u) {
                     tab = res;
                     unk = ux;
@@ -639,7 +645,7 @@ __global__ void __launch_bounds__(NL) k_ures(ChainLaunch A) {
         }
         const SegState* qs = &A.st[nonempty_pred(A, item)];
         const uint32_t t = qs->table[tid];
-        const bool u = (t & STAB_UNKNOWN) && !(t & STAB_CONST);
+        const bool u = (t & STAB_UNKNOWN) && !(t & STAB_CONST) && qs->unk_exit[tid] != ~0ull;
         if (tid == 0) any = 0;
         __syncthreads();
         if (u) any = 1;
@@ -657,6 +663,7 @@ __global__ void __launch_bounds__(NL) k_ures(ChainLaunch A) {
 #pragma unroll
             for (int j = 0; j < NL / 32; j++) {
                 const uint32_t tj = qs->table[lane + 32 * j];
+                // ~0: the predecessor's chain in this slot never ran (nothing to follow)
                 up[j] = ((tj & STAB_UNKNOWN) && !(tj & STAB_CONST)) ? qs->unk_exit[lane + 32 * j] : ~0ull;
             }
             uint32_t nu = 0;
@@ -671,7 +678,7 @@ __global__ void __launch_bounds__(NL) k_ures(ChainLaunch A) {
                     todo = __ballot_sync(FULL, up[j] != ~0ull);
                     uint64_t ux;
                     const uint32_t res = stitch_walk<RULE>(A, S, R, P, sh.ht, sh.X, sh.cnt, seg_lo, seg_hi, flo, fhi,
-                                                           last, e, &ux);
+                                                           last, e, &ux, item);
                     if (lane == 0) {
                         me->ures_pos[nu] = e;
                         me->ures_exit[nu] = ux;

@@ -89,3 +89,65 @@ def test_batch_all_empty_files(ck):
     a = torch.zeros(16, dtype=torch.uint8, device="cuda")
     b, idx = ck.chunk_batch(a, torch.from_numpy(off).cuda(), "ram", 10, 1, 100)
     assert b.numel() == 0 and idx.cpu().numpy().tolist() == [0] * 6
+
+
+def test_autotune_keeps_results(ck):
+    """The autotuner only picks segment size and warp-chain threshold: the
+    boundaries after tuning equal those before (stream and batch forms)."""
+    import torch
+    from paper_2508_05797_gb300 import Chunker
+    from paper_2508_05797_gb300.cdc import OPT_SEGMENT, OPT_WARP_CHAINS
+    c = Chunker(0)
+    try:
+        data = torch.from_numpy(synth.mixed_range(1, 4 << 30, 7 << 20, 24 << 20)).cuda()
+        for alg in ("ram", "ae", "maxp"):
+            w, mn, mx = params("mixed_4g_seed1", alg, 8192)
+            before = c.chunk(data, alg, w, mn, mx).clone()
+            seg, wc, ms = c.autotune(data, alg, w, mn, mx)
+            assert ms > 0 and c.get_option(OPT_SEGMENT) == seg and c.get_option(OPT_WARP_CHAINS) == wc
+            assert torch.equal(c.chunk(data, alg, w, mn, mx), before)
+        arena, off = _files(9, 500, 40_000, 1.5, 4 << 20)
+        w, mn, mx = params("mixed_4g_seed1", "maxp", 8192)
+        b0, i0 = _run(c, arena, off, "maxp", w, mn, mx)
+        a = torch.from_numpy(arena).cuda()
+        d_off = torch.from_numpy(off).cuda()
+        c.autotune(a, "maxp", w, mn, mx, file_off=d_off)
+        b1, i1 = _run(c, arena, off, "maxp", w, mn, mx)
+        assert np.array_equal(b0, b1) and np.array_equal(i0, i1)
+    finally:
+        c.close()
+
+
+def test_batch_graph_replay_matches(ck):
+    """The batched call captured in a CUDA graph (workspace reserved first)
+    and replayed gives the direct call's boundaries."""
+    import torch
+    from paper_2508_05797_gb300 import Chunker
+    arena, off = _files(11, 2000, 20_000, 1.5, 2 << 20)
+    w, mn, mx = params("mixed_4g_seed1", "ram", 8192)
+    expect, eidx = _run(ck, arena, off, "ram", w, mn, mx)
+    c = Chunker(0)
+    try:
+        a = torch.from_numpy(arena).cuda()
+        d_off = torch.from_numpy(off).cuda()
+        n_files = off.size - 1
+        c.reserve("ram", w, mn, mx, arena.size, n_files)
+        out = torch.full((arena.size // mn + n_files + 1,), -1, dtype=torch.int64, device="cuda")
+        idx = torch.empty(n_files + 1, dtype=torch.int64, device="cuda")
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            c.chunk_batch(a, d_off, "ram", w, mn, mx, out=out, index=idx, stream=s, sync=False)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            c.chunk_batch(a, d_off, "ram", w, mn, mx, out=out, index=idx, stream=s, sync=False)
+        for _ in range(2):
+            out.fill_(-1)
+            g.replay()
+            torch.cuda.synchronize()
+            c.sync_status()
+            i = idx.cpu().numpy()
+            assert np.array_equal(i, eidx)
+            assert np.array_equal(out[:int(i[-1])].cpu().numpy().astype(np.uint64), expect)
+    finally:
+        c.close()
