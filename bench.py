@@ -241,14 +241,15 @@ def batched_workload(dev, n_files: int = 100_000, warmup: int = 2, reps: int = 3
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
             ck.chunk_batch(arena, d_off, alg, w, mn, mx, out=out, index=idx, stream=stream, sync=False)
-        for _ in range(warmup):
-            g.replay()
-        torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            g.replay()
-        e1.record(stream)
+        with torch.cuda.stream(stream):  # replay() launches on the current stream
+            for _ in range(warmup):
+                g.replay()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                g.replay()
+            e1.record(stream)
         torch.cuda.synchronize()
         ck.sync_status(stream)
         batch_ms = e0.elapsed_time(e1) / reps
@@ -285,6 +286,68 @@ def batched_workload(dev, n_files: int = 100_000, warmup: int = 2, reps: int = 3
     del arena
     torch.cuda.empty_cache()
     return res
+
+
+def serving_workload(host_stream, dev, n_req: int = 20000, rates=(0.25, 0.5, 0.75, 0.9), slots: int = 4,
+                     budget: int = 40 << 30):
+    """The serving loop: requests with log-normal sizes (median 64 KiB, sigma
+    1.5, clipped to 4 KiB .. 64 MiB, seed 4) cut from the pinned host copy of
+    the mixed stream, algorithm uniform over RAM / AE / MAXP at 8 KiB mean,
+    through cdc_server_* (40 GiB device budget, continuous batching on `slots`
+    streams). First all requests at once (saturation throughput), then Poisson
+    arrivals (seed 5) at fractions of that request rate; per rate the latency
+    from arrival to boundaries in host memory (p50 / p99) and GB/s."""
+    import numpy as np
+
+    import synth
+    from paper_2508_05797_gb300 import Server
+
+    hnp = host_stream.numpy()
+    sizes = synth.lognormal_sizes(4, n_req, 65536, 1.5, 4096, 64 * MIB).astype(np.int64)
+    algs = synth.choice(4, n_req, 3)
+    starts = (synth.lognormal_sizes(6, n_req, 1 << 30, 4.0, 0, hnp.size) % np.maximum(1, hnp.size - sizes)).astype(
+        np.int64)
+    t = wtable()["mixed_4g_seed1"]
+    prm = [(a, t[a]["8192"]["w"], t[a]["8192"]["min"], t[a]["8192"]["max"]) for a in ALGS]
+    outs = [np.zeros(int(sizes[i]) // prm[int(algs[i])][2] + 2, dtype=np.uint64) for i in range(n_req)]
+    total = int(sizes.sum())
+
+    def run(arrivals):
+        srv = Server(dev.index, budget, slots)
+        try:
+            # arrival times start after the submission loop (about 20 us per request)
+            t0 = srv.clock() + 50.0 + 0.03 * n_req
+            for i in range(n_req):
+                a, w, mn, mx = prm[int(algs[i])]
+                srv.submit(hnp[int(starts[i]):int(starts[i]) + int(sizes[i])], a, w, mn, mx, outs[i], tag=i,
+                           arrive_ms=t0 + float(arrivals[i]))
+            res = []
+            while len(res) < n_req:
+                res.extend(srv.poll(4096, wait_ms=100))
+        finally:
+            srv.close()
+        ok = all(r["status"] == 0 for r in res)
+        arr = np.array([r["t_arrive_ms"] for r in res])
+        done = np.array([r["t_done_ms"] for r in res])
+        lat = done - arr
+        span = (done.max() - arr.min()) / 1e3
+        return {"GBps": round(total / span / 1e9, 2), "req_per_s": round(n_req / span, 1),
+                "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "mean_batch": round(float(np.mean([r["batch_size"] for r in res])), 1), "all_ok": ok}
+
+    sat = run(np.zeros(n_req))  # every request arrives at once
+    out = {"workload": "%d requests, log-normal sizes (median 64 KiB, sigma 1.5, 4 KiB..64 MiB, seed 4), "
+                       "%.2f GB from pinned host memory, RAM/AE/MAXP uniform at 8 KiB mean, %d GiB budget, %d slots"
+                       % (n_req, total / 1e9, budget >> 30, slots),
+           "saturation": sat, "rates": []}
+    for f in rates:
+        rate = f * sat["req_per_s"]
+        arrivals = synth.poisson_arrivals(5, n_req, rate / 1e3)  # ms
+        r = run(arrivals)
+        r["offered_req_per_s"] = round(rate, 1)
+        r["offered_fraction"] = f
+        out["rates"].append(r)
+    return out
 
 
 def run_reference(args, rank, world):
@@ -329,6 +392,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--batched-files", type=int, default=100_000)
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--serving-requests", type=int, default=20_000)
     ap.add_argument("--algs", default=",".join(ALGS), help="subset of ram,ae,maxp (profiling cases)")
     ap.add_argument("--means", default=",".join(map(str, MEANS)), help="subset of 4096,8192,16384")
     ap.add_argument("--len-mib", type=int, default=STREAM_LEN // MIB,
@@ -454,6 +519,8 @@ def main():
         line["e2e"] = {"value": round(ncfg * n * e2e_steps * world / dt / 1e9, 2), "unit": "GB/s",
                        "h2d_bytes_per_step": ncfg * n, "d2h_bytes_per_step": int(d2h),
                        "steps": e2e_steps}
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_workload(host, dev, n_req=args.serving_requests)
     if rank == 0 and not args.no_batched:
         for ck in handles:
             ck.close()

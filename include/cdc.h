@@ -250,6 +250,61 @@ CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
 CDC_API cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
                                     uint64_t* out_bounds, size_t* n, cdc_stream stream);
 
+/* ---- serving: requests from host memory, continuous batching --------------
+ *
+ * The paper has no counterpart (it chunks one stream on a CPU). A server owns
+ * `slots` execution slots on one device, each with its own stream, handle
+ * (workspace kept on the device), arena and pinned staging, all allocated at
+ * creation within `budget_bytes` (each slot's share holds its arena for
+ * request bytes, a boundary buffer of arena/1024 + max_batch + 1 entries and
+ * the library's workspace for a full arena). Requests become eligible at their
+ * arrival time; whenever a slot is free, a worker thread packs the eligible
+ * requests that share the oldest one's algorithm and parameters (oldest first,
+ * up to max_batch requests and the slot's capacity) into one batched call:
+ * one copy in per request, one cdc_chunk_batch, one copy of the boundaries
+ * out. Requests arriving meanwhile join later batches; batches on different
+ * slots overlap on the device. Results are those of cdc_chunk on each
+ * request's bytes alone.
+ */
+typedef struct cdc_server_s* cdc_server;
+
+typedef struct {
+    uint64_t tag;        /* the caller's id from cdc_server_submit */
+    uint64_t n_bounds;   /* boundaries of the request (copied out if they fit) */
+    double t_arrive_ms;  /* arrival, submission, start of its batch and */
+    double t_submit_ms;  /* completion, in ms on the server's clock */
+    double t_start_ms;   /* (cdc_server_clock) */
+    double t_done_ms;
+    int32_t status;      /* cdc_status of the request */
+    int32_t alg;
+    uint32_t batch_size; /* requests in its batch */
+    uint32_t pad;
+} cdc_result;
+
+/* budget_bytes >= 64 MiB; 1 <= slots <= 64; max_batch 0 = 4096. Allocates
+ * everything up front (CDC_ERR_NOMEM if it does not fit). */
+CDC_API cdc_status cdc_server_create(cdc_server* out, int device, size_t budget_bytes, int slots, size_t max_batch);
+
+/* Queue a request: len bytes at host_data (pinned memory is fastest; it must
+ * stay valid and unchanged until the request completes), boundaries into
+ * host_bounds (capacity entries; CDC_ERR_CAPACITY in the result, with
+ * n_bounds set, if they do not fit). It becomes eligible at arrive_ms on the
+ * server's clock (earlier values, e.g. 0 or -1: now). Parameters as for
+ * cdc_chunk with min >= 64; CDC_ERR_CAPACITY here if len exceeds a slot's
+ * arena or len / min + 1 its boundary buffer. */
+CDC_API cdc_status cdc_server_submit(cdc_server s, cdc_alg alg, cdc_params p, const uint8_t* host_data, size_t len,
+                                     uint64_t* host_bounds, size_t capacity, uint64_t tag, double arrive_ms);
+
+/* Up to max finished requests (waiting up to wait_ms for the first); *n is
+ * the number returned. Returns a sticky error of the engine, else CDC_OK. */
+CDC_API cdc_status cdc_server_poll(cdc_server s, cdc_result* out, int max, int* n, int wait_ms);
+
+/* The server's clock: ms since cdc_server_create. */
+CDC_API cdc_status cdc_server_clock(cdc_server s, double* now_ms);
+
+/* Finishes the queued requests, then frees everything. */
+CDC_API cdc_status cdc_server_destroy(cdc_server s);
+
 CDC_API const char* cdc_status_string(cdc_status s);
 
 #ifdef __cplusplus

@@ -3,9 +3,9 @@
 The work runs in libcdc.so (CUDA; C ABI in include/cdc.h); this package is
 its Python binding. See ``cdc.Chunker`` and ``cdc.chunk``.
 """
-from .cdc import (ALGS, STATIC_MAX_LEN, CdcError, Chunker, Params, chunk, chunk_batch, chunk_static,
+from .cdc import (ALGS, STATIC_MAX_LEN, CdcError, Chunker, Params, Server, chunk, chunk_batch, chunk_static,
                   default_chunker, exported_symbols, library_path, load_library, max_boundaries)
 
-__all__ = ["ALGS", "STATIC_MAX_LEN", "CdcError", "Chunker", "Params", "chunk", "chunk_batch", "chunk_static",
+__all__ = ["ALGS", "STATIC_MAX_LEN", "CdcError", "Chunker", "Params", "Server", "chunk", "chunk_batch", "chunk_static",
            "default_chunker",
            "exported_symbols", "library_path", "load_library", "max_boundaries"]

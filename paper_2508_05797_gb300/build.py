@@ -19,9 +19,9 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-              "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]
-SOURCES = ["api.cu", "summarize.cu", "chain.cu", "batch.cu"]
-HEADERS = ["chain_logic.cuh", "cdc_device.cuh", "cdc_launch.h"]
+              "--expt-relaxed-constexpr", "-Xcompiler", "-pthread", "-I", CSRC, "-I", INCLUDE]
+SOURCES = ["api.cu", "summarize.cu", "chain.cu", "batch.cu", "serve.cu"]
+HEADERS = ["chain_logic.cuh", "cdc_device.cuh", "cdc_launch.h", "warp_rules.cuh", "warp_fast.cuh"]
 
 
 def nvcc() -> str:
@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [cc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+    cmd = [cc] + ARCH + ["-shared", "-cudart", "static", "-Xcompiler", "-pthread", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

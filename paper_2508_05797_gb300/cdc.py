@@ -39,6 +39,14 @@ class Params(ctypes.Structure):
     _fields_ = [("w", ctypes.c_uint32), ("min", ctypes.c_uint32), ("max", ctypes.c_uint32)]
 
 
+class Result(ctypes.Structure):
+    """cdc_result: one finished serving request."""
+    _fields_ = [("tag", ctypes.c_uint64), ("n_bounds", ctypes.c_uint64), ("t_arrive_ms", ctypes.c_double),
+                ("t_submit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double),
+                ("status", ctypes.c_int32), ("alg", ctypes.c_int32), ("batch_size", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -76,6 +84,11 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "cdc_chunk_static": ([i32, P, vp, sz, vp, ctypes.POINTER(sz), vp], i32),
             "cdc_autotune": ([vp, i32, P, vp, sz, vp, sz, vp, vp, sz, ctypes.POINTER(i64), ctypes.POINTER(i64),
                               ctypes.POINTER(ctypes.c_float), vp], i32),
+            "cdc_server_create": ([ctypes.POINTER(vp), i32, sz, i32, sz], i32),
+            "cdc_server_submit": ([vp, i32, P, vp, sz, vp, sz, u64, ctypes.c_double], i32),
+            "cdc_server_poll": ([vp, ctypes.POINTER(Result), i32, ctypes.POINTER(i32), i32], i32),
+            "cdc_server_clock": ([vp, ctypes.POINTER(ctypes.c_double)], i32),
+            "cdc_server_destroy": ([vp], i32),
             "cdc_status_string": ([i32], ctypes.c_char_p),
         }
         for name, (args, res) in sig.items():
@@ -89,7 +102,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return ["cdc_create", "cdc_destroy", "cdc_chunk", "cdc_chunk_async", "cdc_chunk_batch", "cdc_chunk_host",
             "cdc_reserve", "cdc_sync_status", "cdc_set_option", "cdc_get_option", "cdc_last_timing",
-            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_status_string"]
+            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_server_create", "cdc_server_submit",
+            "cdc_server_poll", "cdc_server_clock", "cdc_server_destroy", "cdc_status_string"]
 
 
 def alg_id(alg) -> int:
@@ -247,6 +261,59 @@ class Chunker:
 
     def sync_status(self, stream=None):
         _check(self.lib.cdc_sync_status(self.h, _stream_handle(stream)), "device-side status")
+
+
+class Server:
+    """Serving engine (cdc_server_*): requests from host memory, admitted under
+    a device-memory budget and run with continuous batching on `slots` streams.
+    Submitted arrays must stay alive and unchanged until their result is
+    polled (the binding keeps references until then)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 40 << 30, slots: int = 4, max_batch: int = 0):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        _check(self.lib.cdc_server_create(ctypes.byref(h), device, budget_bytes, slots, max_batch),
+               "cdc_server_create")
+        self.h = h
+        self._live = {}
+
+    def submit(self, data, alg, w: int, mn: int, mx: int, out, tag: int, arrive_ms: float = -1.0):
+        """Queue `data` (uint8 numpy array) with boundaries into `out` (uint64)."""
+        import numpy as np
+        assert data.dtype == np.uint8 and data.flags.c_contiguous
+        assert out.dtype == np.uint64 and out.flags.c_contiguous
+        _check(self.lib.cdc_server_submit(self.h, alg_id(alg), Params(w, mn, mx), data.ctypes.data if data.size else None,
+                                          data.size, out.ctypes.data if out.size else None, out.size, int(tag),
+                                          float(arrive_ms)), "cdc_server_submit")
+        self._live[int(tag)] = (data, out)
+
+    def poll(self, max_results: int = 1024, wait_ms: int = 0) -> list:
+        arr = (Result * max(max_results, 1))()
+        n = ctypes.c_int()
+        _check(self.lib.cdc_server_poll(self.h, arr, max_results, ctypes.byref(n), wait_ms), "cdc_server_poll")
+        out = []
+        for i in range(n.value):
+            r = arr[i]
+            self._live.pop(int(r.tag), None)
+            out.append({f: getattr(r, f) for f, _ in Result._fields_ if f != "pad"})
+        return out
+
+    def clock(self) -> float:
+        t = ctypes.c_double()
+        _check(self.lib.cdc_server_clock(self.h, ctypes.byref(t)), "cdc_server_clock")
+        return t.value
+
+    def close(self):
+        if self.h:
+            self.lib.cdc_server_destroy(self.h)
+            self.h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 _default: dict = {}

@@ -68,6 +68,23 @@ struct ChainLaunch {
     uint32_t warp_chains;    // per-thread speculation rounds run while more chains than this are alive
 };
 
+// Memo of per-device launch properties: fn(arg) runs once per (device, key, arg).
+int launch_memo(int key, uint32_t arg, int (*fn)(uint32_t));
+
+// Let `kernel` take any dynamic shared memory the current device allows
+// (launches still request only what they use). Returns a cudaError_t.
+template <typename K>
+int allow_max_smem(K kernel) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return (int)e;
+}
+
 int summary_max_smem();
 int summary_maxp_smem(uint32_t halo_blocks);
 uint32_t maxp_halo_blocks(uint32_t w);

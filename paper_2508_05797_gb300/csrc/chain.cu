@@ -33,6 +33,8 @@
 #include "cdc_launch.h"
 #include "warp_fast.cuh"
 
+#include <mutex>
+
 namespace cdc {
 
 // ---- per-segment state --------------------------------------------------------
@@ -1070,14 +1072,46 @@ int chain_smem(int rule, uint32_t win) {
     return 16;
 }
 
+// Per-device memo of launch properties (function attributes set, occupancy),
+// so that a call does not repeat those driver queries.
+static std::mutex g_memo_mu;
+struct Memo {
+    int dev, key;
+    uint32_t arg;
+    int val;
+};
+static constexpr int kMemoCap = 512;
+static Memo g_memo[kMemoCap];
+static int g_memo_n = 0;
+
+int launch_memo(int key, uint32_t arg, int (*fn)(uint32_t)) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lock(g_memo_mu);
+        for (int i = 0; i < g_memo_n; i++)
+            if (g_memo[i].dev == dev && g_memo[i].key == key && g_memo[i].arg == arg) return g_memo[i].val;
+    }
+    const int v = fn(arg);
+    std::lock_guard<std::mutex> lock(g_memo_mu);
+    if (g_memo_n < kMemoCap) g_memo[g_memo_n++] = Memo{dev, key, arg, v};
+    return v;
+}
+
+template <int RULE>
+int allow_smem() {
+    return launch_memo(100 + RULE, 0, [](uint32_t) {
+        int e = allow_max_smem(k_spec<RULE>);
+        return e == (int)cudaSuccess ? allow_max_smem(k_output<RULE>) : e;
+    });
+}
+
 template <int RULE>
 static cudaError_t launch_rule(const ChainLaunch& a, const ChainGrids& gr, cudaStream_t st, int* launches,
                                cudaEvent_t ev_spec) {
     int sm = chain_smem(RULE, a.win);
-    cudaError_t e = cudaFuncSetAttribute(k_spec<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_output<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e != cudaSuccess) return e;
+    const int set = allow_smem<RULE>();
+    if (set != (int)cudaSuccess) return (cudaError_t)set;
     k_spec<RULE><<<gr.spec, NL, sm, st>>>(a);
     if (ev_spec) cudaEventRecord(ev_spec, st);
     k_stitch<RULE><<<gr.stitch, NL, 0, st>>>(a);
@@ -1104,10 +1138,12 @@ cudaError_t launch_chain(const ChainLaunch& a, int rule, const ChainGrids& gr, c
 
 template <int RULE>
 static int occ_spec(uint32_t win) {
-    int sm = chain_smem(RULE, win), n = 0;
-    cudaFuncSetAttribute(k_spec<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spec<RULE>, NL, sm);
-    return n > 0 ? n : 1;
+    allow_smem<RULE>();
+    return launch_memo(200 + RULE, win, [](uint32_t wn) {
+        int sm = chain_smem(RULE, wn), n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spec<RULE>, NL, sm);
+        return n > 0 ? n : 1;
+    });
 }
 
 int spec_blocks_per_sm(int rule, uint32_t win) {

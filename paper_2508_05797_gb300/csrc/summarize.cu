@@ -334,23 +334,21 @@ int summary_maxp_smem(uint32_t halo_blocks) {
 
 uint32_t maxp_halo_blocks(uint32_t w) { return (w + 63) / 64 + 1; }
 
+static int allow_summary_smem(int kind) {
+    if (kind == SUM_MAXP) return launch_memo(300, 0, [](uint32_t) { return allow_max_smem(k_summary_maxp); });
+    if (kind == SUM_MAX_INV) return launch_memo(301, 0, [](uint32_t) { return allow_max_smem(k_summary_max<true>); });
+    return launch_memo(302, 0, [](uint32_t) { return allow_max_smem(k_summary_max<false>); });
+}
+
 cudaError_t launch_summary(const SumLaunch& a, int kind, int grid, cudaStream_t st) {
+    const int set = allow_summary_smem(kind);
+    if (set != (int)cudaSuccess) return (cudaError_t)set;
     if (kind == SUM_MAXP) {
-        int sm = summary_maxp_smem(a.halo_blocks);
-        cudaError_t e = cudaFuncSetAttribute(k_summary_maxp, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (e != cudaSuccess) return e;
-        k_summary_maxp<<<grid, MP_THREADS, sm, st>>>(a);
+        k_summary_maxp<<<grid, MP_THREADS, summary_maxp_smem(a.halo_blocks), st>>>(a);
+    } else if (kind == SUM_MAX_INV) {
+        k_summary_max<true><<<grid, S1_THREADS, summary_max_smem(), st>>>(a);
     } else {
-        int sm = summary_max_smem();
-        if (kind == SUM_MAX_INV) {
-            cudaError_t e = cudaFuncSetAttribute(k_summary_max<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-            if (e != cudaSuccess) return e;
-            k_summary_max<true><<<grid, S1_THREADS, sm, st>>>(a);
-        } else {
-            cudaError_t e = cudaFuncSetAttribute(k_summary_max<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-            if (e != cudaSuccess) return e;
-            k_summary_max<false><<<grid, S1_THREADS, sm, st>>>(a);
-        }
+        k_summary_max<false><<<grid, S1_THREADS, summary_max_smem(), st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -361,17 +359,18 @@ cudaError_t launch_reset(Ctrl* ctrl, cudaStream_t st) {
 }
 
 int summary_blocks_per_sm(int kind, uint32_t halo_blocks) {
-    int n = 0;
-    if (kind == SUM_MAXP) {
-        int sm = summary_maxp_smem(halo_blocks);
-        cudaFuncSetAttribute(k_summary_maxp, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_summary_maxp, MP_THREADS, sm);
-    } else {
-        int sm = summary_max_smem();
-        cudaFuncSetAttribute(k_summary_max<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_summary_max<false>, S1_THREADS, sm);
-    }
-    return n > 0 ? n : 1;
+    allow_summary_smem(kind);
+    if (kind == SUM_MAXP)
+        return launch_memo(310, halo_blocks, [](uint32_t hb) {
+            int n = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_summary_maxp, MP_THREADS, summary_maxp_smem(hb));
+            return n > 0 ? n : 1;
+        });
+    return launch_memo(311, 0, [](uint32_t) {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_summary_max<false>, S1_THREADS, summary_max_smem());
+        return n > 0 ? n : 1;
+    });
 }
 
 uint64_t summary_tiles(int kind, uint64_t nblk) {
