@@ -394,8 +394,11 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                     if (sh.fill >= (unsigned)HFILL) stat_add(A, STAT_HASH_FULL, 1);
                 }
             }
-            // the last few chains, one warp each (every step shared by the 32 lanes)
-            for (unsigned q = (unsigned)(tid >> 5); q < sh.nq; q += NW) {
+            // the last chains, one warp each (every step shared by the 32 lanes);
+            // a warp that finishes a chain takes the next one
+            if (tid == 0) sh.nq2 = NW;
+            __syncthreads();
+            for (unsigned q = (unsigned)(tid >> 5); q < sh.nq;) {
                 const unsigned l = sh.q_lane[buf][q];
                 uint64_t v = sh.q_s[buf][q];
                 uint32_t cc = sh.q_c[buf][q];
@@ -436,7 +439,9 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                         sh.X[l] = v;
                         sh.cnt[l] = cc;
                     }
+                    q = atomicAdd(&sh.nq2, 1u);
                 }
+                q = __shfl_sync(FULL, q, 0);
             }
         }
         if (empty) {
