@@ -202,9 +202,8 @@ CDC_API cdc_status cdc_profile_collect(cdc_handle h, int* calls, double* summary
  * resolution, output steps, empty segments, chains handed to whole warps,
  * then clock cycles summed over segments (set-up, speculation, merge
  * resolution, stitching), per-thread rounds, the cycles of the rounds and of
- * the one-warp-per-chain phase, the cycles inside that phase's chain steps and
- * hash inserts, the hash slots those inserts probed, stitch walks of more than
- * 64 steps, and (steps << 32 | segment) of the longest one (24 counters).
+ * the one-warp-per-chain phase, stitch walks of more than 64 steps, and
+ * (steps << 32 | segment) of the longest one (21 counters).
  * Synchronises `stream`. */
 CDC_API cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream stream);
 

@@ -20,7 +20,7 @@ struct Ctrl {
     unsigned int err;            // sticky error bits, cleared by the host
     unsigned int stats_on;       // 1: kernels accumulate the counters below
     unsigned int pad[5];
-    unsigned long long stats[24];  // see STAT_* (reset by the host)
+    unsigned long long stats[21];  // see STAT_* (reset by the host)
 };
 enum : int {
     STAT_SEGMENTS = 0,      // non-empty segments speculated
@@ -42,12 +42,9 @@ enum : int {
     STAT_ROUNDS = 16,       // per-thread rounds (summed over segments)
     STAT_CYC_ROUNDS = 17,   //   their cycles (part of STAT_CYC_THREADS)
     STAT_CYC_SURV = 18,     // cycles of the one-warp-per-chain phase (part of STAT_CYC_THREADS)
-    STAT_CYC_WSTEP = 19,    // cycles inside whole-warp chain steps of that phase (summed over steps)
-    STAT_CYC_WHASH = 20,    // cycles of their position-hash inserts
-    STAT_PROBES = 21,       // hash slots probed by those inserts
-    STAT_STITCH_LONG = 22,  // stitch walks of more than 64 steps
-    STAT_STITCH_MAXW = 23,  // (steps << 32) | segment of the longest stitch walk
-    STAT_N = 24
+    STAT_STITCH_LONG = 19,  // stitch walks of more than 64 steps
+    STAT_STITCH_MAXW = 20,  // (steps << 32) | segment of the longest stitch walk
+    STAT_N = 21
 };
 enum : unsigned int { ERR_TIMEOUT = 1u, ERR_INTERNAL = 2u };
 

@@ -160,13 +160,11 @@ __device__ __forceinline__ uint32_t hslot(uint32_t key) { return (key * 26544357
 constexpr uint32_t H_INSERTED = 0xFFFFFFFFu, H_FULL = 0xFFFFFFFEu;
 
 // insert; returns H_INSERTED, H_FULL, or the value already stored for key
-__device__ __forceinline__ uint32_t hinsert(unsigned long long* ht, unsigned int* fill, uint32_t key, uint32_t val,
-                                            uint32_t* probes = nullptr) {
+__device__ __forceinline__ uint32_t hinsert(unsigned long long* ht, unsigned int* fill, uint32_t key, uint32_t val) {
     if (*reinterpret_cast<volatile unsigned int*>(fill) >= (unsigned)HFILL) return H_FULL;
     const unsigned long long ent = ((unsigned long long)key << 32) | val;
     uint32_t s = hslot(key);
     for (int i = 0; i < 64; i++) {
-        if (probes) (*probes)++;
         unsigned long long prev = atomicCAS(&ht[s], 0ull, ent);
         if (prev == 0ull) {
             atomicAdd(fill, 1u);
@@ -406,15 +404,11 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                 int qmg = -1;
                 uint32_t qmi = 0;
                 while (v < seg_hi) {
-                    const long long c0 = A.stats ? clock64() : 0;
                     if (recq) {
                         uint32_t hr = H_FULL;
-                        uint32_t probes = 0;
                         if (lane == 0 && cc < 0xFFFFu)
-                            hr = hinsert(sh.ht, &sh.fill, (uint32_t)(v - seg_lo) + 1u, (l << 16) | cc, &probes);
+                            hr = hinsert(sh.ht, &sh.fill, (uint32_t)(v - seg_lo) + 1u, (l << 16) | cc);
                         hr = __shfl_sync(FULL, hr, 0);
-                        if (A.stats && lane == 0) stat_add(A, STAT_PROBES, probes);
-                        if (A.stats && lane == 0) stat_add(A, STAT_CYC_WHASH, (unsigned long long)(clock64() - c0));
                         if (hr == H_FULL) {
                             recq = false;
                         } else if (hr != H_INSERTED) {
@@ -425,11 +419,9 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                     }
                     uint32_t k;
                     uint64_t dd;
-                    const long long c1 = A.stats ? clock64() : 0;
                     v = f_advance<RULE>(W, S, R, P, flo, fhi, v, seg_hi, &k, &dd);
                     cc += k;
                     if (lane == 0) stat_add(A, STAT_WARP_STEPS, 1);
-                    if (A.stats && lane == 0) stat_add(A, STAT_CYC_WSTEP, (unsigned long long)(clock64() - c1));
                 }
                 if (lane == 0) {
                     sh.mg[l] = qmg;
