@@ -154,13 +154,12 @@ def dist_setup(n_gpus):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
-        try:
-            import torch
+        # one process per GPU over NCCL; gloo where there is no GPU (host-side tests)
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
             torch.cuda.set_device(local)
-        except Exception:
-            pass
         dist.init_process_group(backend=backend)
     return rank, world, local
 
@@ -176,7 +175,8 @@ def allreduce_max(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -355,7 +355,7 @@ def run_reference(args, rank, world):
         return 0
     import oracle
     import synth
-    sample = 32 * MIB
+    sample = args.ref_sample_mib * MIB
     data = synth.mixed_range(1, STREAM_LEN, 0, sample)
     cfg = configs()
 
@@ -376,7 +376,8 @@ def run_reference(args, rank, world):
             "data": "synthetic (seeded)",
             "config": {"workload": WORKLOAD, "sample_bytes_per_step": 9 * sample},
             "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": "first 32 MiB of the 4 GiB mixed stream per (alg, mean) pair, one thread"},
+                             "sample": "first %d MiB of the 4 GiB mixed stream per (alg, mean) pair, one thread"
+                                       % args.ref_sample_mib},
             "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -393,6 +394,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--batched-files", type=int, default=100_000)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--ref-sample-mib", type=int, default=32, help="reference arm: bytes per (alg, mean) pair")
     ap.add_argument("--serving-requests", type=int, default=20_000)
     ap.add_argument("--algs", default=",".join(ALGS), help="subset of ram,ae,maxp (profiling cases)")
     ap.add_argument("--means", default=",".join(map(str, MEANS)), help="subset of 4096,8192,16384")
