@@ -394,6 +394,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--batched-files", type=int, default=100_000)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--streams", type=int, default=3, help="streams the nine calls of a step are spread over")
     ap.add_argument("--ref-sample-mib", type=int, default=32, help="reference arm: bytes per (alg, mean) pair")
     ap.add_argument("--serving-requests", type=int, default=20_000)
     ap.add_argument("--algs", default=",".join(ALGS), help="subset of ram,ae,maxp (profiling cases)")
@@ -429,10 +430,26 @@ def main():
         outs.append(torch.empty(n // mn + 1, dtype=torch.int64, device=dev))
         counts.append(torch.zeros(1, dtype=torch.int64, device=dev))
     stream = torch.cuda.current_stream(dev)
+    # the nine calls are independent (one handle each): spread them over a few
+    # streams so that one call's latency-bound kernels overlap another's
+    nstreams = max(1, args.streams)
+    side = [torch.cuda.Stream(dev) for _ in range(nstreams)]
+    fork = [torch.cuda.Event() for _ in range(nstreams)]
+    join = [torch.cuda.Event() for _ in range(nstreams)]
 
     def step():
-        for (alg, mean, w, mn, mx), ck, o, c in zip(cfg, handles, outs, counts):
-            ck.chunk_async(data, alg, w, mn, mx, o, c, stream=stream)
+        if nstreams == 1:
+            for (alg, mean, w, mn, mx), ck, o, c in zip(cfg, handles, outs, counts):
+                ck.chunk_async(data, alg, w, mn, mx, o, c, stream=stream)
+            return
+        for i in range(nstreams):
+            fork[i].record(stream)
+            side[i].wait_event(fork[i])
+        for k, ((alg, mean, w, mn, mx), ck, o, c) in enumerate(zip(cfg, handles, outs, counts)):
+            ck.chunk_async(data, alg, w, mn, mx, o, c, stream=side[k % nstreams])
+        for i in range(nstreams):
+            join[i].record(side[i])
+            stream.wait_event(join[i])
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -499,6 +516,7 @@ def main():
                        "%s; subset algs=%s means=%s, first %d MiB" % (WORKLOAD, args.algs, args.means, args.len_mib),
                        "bytes_per_step": ncfg * n,
                        "l2": "inputs larger than L2 (4 GiB per call, 129 MB L2)",
+                       "streams": nstreams,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_frac": round(gbs / world / peak, 4), "per_alg": per_alg, "roofline": roofline,
             "gpu_launches": int(launches), "clocks": clocks}
