@@ -350,6 +350,47 @@ def serving_workload(host_stream, dev, n_req: int = 20000, rates=(0.25, 0.5, 0.7
     return out
 
 
+def prims_workload(data, dev, n_q: int = 1 << 20, span: int = 8192, reps: int = 3):
+    """The two processing patterns alone (cdc_ebs, cdc_rs): n_q ranges of
+    `span` bytes at seeded offsets of the 4 GiB stream; Extreme Byte Search
+    for the maximum and its first position, then a GEQ Range Scan for that
+    maximum (so each scan stops at the maximum). GB/s of range bytes."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2508_05797_gb300 import ebs, rs
+
+    n = data.numel()
+    starts = (synth.lognormal_sizes(8, n_q, 1 << 30, 4.0, 0, n) % max(1, n - span)).astype(np.int64)
+    r = torch.from_numpy(np.stack([starts, starts + span], axis=1)).to(dev)
+    out = {"workload": "%d ranges of %d bytes at seeded offsets of the 4 GiB mixed stream" % (n_q, span)}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    v, p = ebs(data, r, "max")
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        v, p = ebs(data, r, "max")
+    e1.record()
+    torch.cuda.synchronize()
+    t_ebs = e0.elapsed_time(e1) / reps
+    q = rs(data, r, v, "geq")
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        q = rs(data, r, v, "geq")
+    e1.record()
+    torch.cuda.synchronize()
+    t_rs = e0.elapsed_time(e1) / reps
+    scanned = int((q - r[:, 0] + 1).clamp(max=span).sum().item())
+    out["ebs"] = {"ms": round(t_ebs, 3), "GBps": round(n_q * span / (t_ebs / 1e3) / 1e9, 1),
+                  "queries_per_s": round(n_q / (t_ebs / 1e3), 0)}
+    out["rs_geq"] = {"ms": round(t_rs, 3), "GBps_of_ranges": round(n_q * span / (t_rs / 1e3) / 1e9, 1),
+                     "GBps_scanned": round(scanned / (t_rs / 1e3) / 1e9, 1),
+                     "same_position": bool(torch.equal(q, p))}
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -394,6 +435,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--batched-files", type=int, default=100_000)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-prims", action="store_true", help="skip the EBS / RS measurement")
     ap.add_argument("--streams", type=int, default=3, help="streams the nine calls of a step are spread over")
     ap.add_argument("--ref-sample-mib", type=int, default=32, help="reference arm: bytes per (alg, mean) pair")
     ap.add_argument("--serving-requests", type=int, default=20_000)
@@ -539,6 +581,8 @@ def main():
         line["e2e"] = {"value": round(ncfg * n * e2e_steps * world / dt / 1e9, 2), "unit": "GB/s",
                        "h2d_bytes_per_step": ncfg * n, "d2h_bytes_per_step": int(d2h),
                        "steps": e2e_steps}
+    if rank == 0 and not args.no_prims:
+        line["prims"] = prims_workload(data, dev)
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_workload(host, dev, n_req=args.serving_requests)
     if rank == 0 and not args.no_batched:

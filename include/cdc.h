@@ -249,6 +249,27 @@ CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
 CDC_API cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
                                     uint64_t* out_bounds, size_t* n, cdc_stream stream);
 
+/* ---- the two processing patterns as standalone device operations -----------
+ *
+ * Extreme Byte Search (Section 3.1) and Range Scan (Section 3.2) over many
+ * byte ranges of one device buffer at once. d_ranges holds 2n offsets
+ * (start, end) into data, each range [start, end) clipped to len; results
+ * are offsets into data. Asynchronous on `stream`; no handle needed.
+ */
+typedef enum { CDC_EBS_MAX = 0, CDC_EBS_MIN = 1 } cdc_ebs_op;
+typedef enum { CDC_RS_GT = 0, CDC_RS_LT = 1, CDC_RS_GEQ = 2, CDC_RS_LEQ = 3, CDC_RS_EQ = 4 } cdc_rs_cmp;
+
+/* d_value[i] = the maximum (CDC_EBS_MAX) or minimum byte of range i and, if
+ * d_pos is not NULL, d_pos[i] = the offset of its first occurrence. An empty
+ * range gives 0 (max) or 255 (min) and its start. */
+CDC_API cdc_status cdc_ebs(cdc_ebs_op op, const uint8_t* data, size_t len, const uint64_t* d_ranges, size_t n,
+                           uint8_t* d_value, uint64_t* d_pos, cdc_stream stream);
+
+/* d_pos[i] = the first offset p in range i with cmp(data[p], d_thresholds[i])
+ * (GT: >, LT: <, GEQ: >=, LEQ: <=, EQ: ==), or the range's end if none. */
+CDC_API cdc_status cdc_rs(cdc_rs_cmp cmp, const uint8_t* data, size_t len, const uint64_t* d_ranges,
+                          const uint8_t* d_thresholds, size_t n, uint64_t* d_pos, cdc_stream stream);
+
 /* ---- serving: requests from host memory, continuous batching --------------
  *
  * The paper has no counterpart (it chunks one stream on a CPU). A server owns

@@ -55,6 +55,10 @@ class Oracle:
         lib.oracle_maxp_is_target.restype = i32
         lib.oracle_maxp_targets.argtypes = [vp, u64, u32, vp, u64]
         lib.oracle_maxp_targets.restype = u64
+        lib.oracle_ebs.argtypes = [i32, vp, u64, u64, u64, ctypes.POINTER(u64)]
+        lib.oracle_ebs.restype = u32
+        lib.oracle_rs.argtypes = [i32, vp, u64, u64, u64, u32]
+        lib.oracle_rs.restype = u64
         self.lib = lib
 
     @staticmethod
@@ -97,6 +101,24 @@ class Oracle:
         n = int(self.lib.oracle_maxp_targets(a.ctypes.data, a.size, w, out.ctypes.data, cap))
         assert n <= cap
         return out[:n].copy()
+
+
+    def ebs(self, op, data, a: int, b: int):
+        """(extreme byte, offset of its first occurrence) of data[a:b]; op 'max' or 'min'."""
+        arr = self._buf(data)
+        pos = ctypes.c_uint64()
+        v = self.lib.oracle_ebs(EBS_OPS[op], arr.ctypes.data if arr.size else None, arr.size, a, b,
+                                ctypes.byref(pos))
+        return int(v), int(pos.value)
+
+    def rs(self, cmp, data, a: int, b: int, t: int) -> int:
+        """First offset in [a, b) whose byte compares true against t, else b."""
+        arr = self._buf(data)
+        return int(self.lib.oracle_rs(RS_CMPS[cmp], arr.ctypes.data if arr.size else None, arr.size, a, b, t))
+
+
+EBS_OPS = {"max": 0, "min": 1}
+RS_CMPS = {"gt": 0, "lt": 1, "geq": 2, "leq": 3, "eq": 4}
 
 
 def get(lib_path: str | None = None) -> Oracle:

@@ -135,3 +135,42 @@ uint64_t oracle_maxp_targets(const uint8_t* B, uint64_t len, uint32_t w,
         }
     return n;
 }
+
+/* Extreme Byte Search (Section 3.1): the maximum (op 0) or minimum (op 1)
+ * byte of B[a, b) and the offset of its first occurrence; an empty range
+ * gives 0 (maximum) or 255 (minimum) at a. Plain loop, one byte at a time. */
+uint32_t oracle_ebs(int op, const uint8_t* B, uint64_t len, uint64_t a, uint64_t b, uint64_t* pos) {
+    if (b > len) b = len;
+    uint32_t best = op == 1 ? 255 : 0;
+    *pos = a;
+    int seen = 0;
+    for (uint64_t i = a; i < b; i++) {
+        const uint32_t v = B[i];
+        if (!seen || (op == 1 ? v < best : v > best)) {
+            best = v;
+            *pos = i;
+            seen = 1;
+        }
+    }
+    return best;
+}
+
+/* Range Scan (Section 3.2): the first offset i in [a, b) whose byte compares
+ * true against t with GT (0), LT (1), GEQ (2), LEQ (3) or EQ (4); b as given
+ * if none (the range is clipped to len for reading). */
+uint64_t oracle_rs(int cmp, const uint8_t* B, uint64_t len, uint64_t a, uint64_t b, uint32_t t) {
+    const uint64_t e = b < len ? b : len;
+    for (uint64_t i = a; i < e; i++) {
+        const uint32_t v = B[i];
+        int hit = 0;
+        switch (cmp) {
+        case 0: hit = v > t; break;
+        case 1: hit = v < t; break;
+        case 2: hit = v >= t; break;
+        case 3: hit = v <= t; break;
+        default: hit = v == t; break;
+        }
+        if (hit) return i;
+    }
+    return b;
+}

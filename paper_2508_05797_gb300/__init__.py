@@ -3,9 +3,10 @@
 The work runs in libcdc.so (CUDA; C ABI in include/cdc.h); this package is
 its Python binding. See ``cdc.Chunker`` and ``cdc.chunk``.
 """
-from .cdc import (ALGS, STATIC_MAX_LEN, CdcError, Chunker, Params, Server, chunk, chunk_batch, chunk_static,
+from .cdc import (ALGS, STATIC_MAX_LEN, CdcError, Chunker, Params, Server, chunk, chunk_batch, chunk_static, ebs, rs,
                   default_chunker, exported_symbols, library_path, load_library, max_boundaries)
 
 __all__ = ["ALGS", "STATIC_MAX_LEN", "CdcError", "Chunker", "Params", "Server", "chunk", "chunk_batch", "chunk_static",
+           "ebs", "rs",
            "default_chunker",
            "exported_symbols", "library_path", "load_library", "max_boundaries"]

@@ -84,6 +84,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "cdc_chunk_static": ([i32, P, vp, sz, vp, ctypes.POINTER(sz), vp], i32),
             "cdc_autotune": ([vp, i32, P, vp, sz, vp, sz, vp, vp, sz, ctypes.POINTER(i64), ctypes.POINTER(i64),
                               ctypes.POINTER(ctypes.c_float), vp], i32),
+            "cdc_ebs": ([i32, vp, sz, vp, sz, vp, vp, vp], i32),
+            "cdc_rs": ([i32, vp, sz, vp, vp, sz, vp, vp], i32),
             "cdc_server_create": ([ctypes.POINTER(vp), i32, sz, i32, sz], i32),
             "cdc_server_submit": ([vp, i32, P, vp, sz, vp, sz, u64, ctypes.c_double], i32),
             "cdc_server_poll": ([vp, ctypes.POINTER(Result), i32, ctypes.POINTER(i32), i32], i32),
@@ -102,7 +104,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return ["cdc_create", "cdc_destroy", "cdc_chunk", "cdc_chunk_async", "cdc_chunk_batch", "cdc_chunk_host",
             "cdc_reserve", "cdc_sync_status", "cdc_set_option", "cdc_get_option", "cdc_last_timing",
-            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_server_create", "cdc_server_submit",
+            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_ebs", "cdc_rs", "cdc_server_create", "cdc_server_submit",
             "cdc_server_poll", "cdc_server_clock", "cdc_server_destroy", "cdc_status_string"]
 
 
@@ -330,6 +332,41 @@ def default_chunker(device: int | None = None) -> Chunker:
 def chunk(data, alg, w: int, mn: int, mx: int, stream=None):
     """Boundaries (int64 CUDA tensor) of a uint8 CUDA tensor on the current stream."""
     return default_chunker(data.device.index).chunk(data, alg, w, mn, mx, stream=stream)
+
+
+EBS_OPS = {"max": 0, "min": 1}
+RS_CMPS = {"gt": 0, "lt": 1, "geq": 2, "leq": 3, "eq": 4}
+
+
+def ebs(data, ranges, op="max", with_pos=True, stream=None):
+    """Extreme Byte Search over ranges (int64 CUDA tensor of shape (n, 2))
+    of a uint8 CUDA tensor: (values uint8, first positions int64 or None)."""
+    import torch
+    assert data.dtype == torch.uint8 and data.is_cuda and data.is_contiguous()
+    r = ranges.contiguous()
+    n = r.shape[0]
+    val = torch.empty(n, dtype=torch.uint8, device=data.device)
+    pos = torch.empty(n, dtype=torch.int64, device=data.device) if with_pos else None
+    _check(load_library().cdc_ebs(EBS_OPS[op], data.data_ptr() if data.numel() else None, data.numel(),
+                                  r.data_ptr() if n else None, n, val.data_ptr() if n else None,
+                                  pos.data_ptr() if (pos is not None and n) else None, _stream_handle(stream)),
+           "cdc_ebs")
+    return val, pos
+
+
+def rs(data, ranges, thresholds, cmp="geq", stream=None):
+    """Range Scan: first position in each range whose byte compares true
+    against its threshold (uint8 CUDA tensor), or the range end."""
+    import torch
+    assert data.dtype == torch.uint8 and data.is_cuda and data.is_contiguous()
+    r = ranges.contiguous()
+    t = thresholds.contiguous()
+    n = r.shape[0]
+    pos = torch.empty(n, dtype=torch.int64, device=data.device)
+    _check(load_library().cdc_rs(RS_CMPS[cmp], data.data_ptr() if data.numel() else None, data.numel(),
+                                 r.data_ptr() if n else None, t.data_ptr() if n else None, n,
+                                 pos.data_ptr() if n else None, _stream_handle(stream)), "cdc_rs")
+    return pos
 
 
 STATIC_MAX_LEN = 16 << 20

@@ -1,0 +1,184 @@
+// prims.cu -- the two processing patterns of hashless chunking as standalone
+// device operations over many byte ranges at once (include/cdc.h, cdc_ebs and
+// cdc_rs):
+//   Extreme Byte Search (Section 3.1): the maximum or minimum byte of a range
+//     and the offset of its first occurrence;
+//   Range Scan (Section 3.2): the first byte of a range that compares GT, LT,
+//     GEQ, LEQ or EQ against a threshold.
+// One warp per range: each lane takes a 16-byte granule per round (512 bytes
+// per warp and round), bytes are compared in 16-bit lanes (a lane add that
+// reaches bit 15 exactly when the byte is >= a threshold; native 16x2 max),
+// the first hit comes from a ballot.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cdc.h"
+#include "chain_logic.cuh"
+
+namespace cdc {
+namespace {
+
+constexpr uint32_t FULLMASK = 0xFFFFFFFFu;
+
+// bytes of granule g (16 bytes at base + 16 g) that lie in [a, b), others
+// replaced by `fill` (a byte value that cannot win)
+__device__ __forceinline__ void load_granule(const uint8_t* base, uint64_t g, uint64_t a, uint64_t b, uint32_t fill,
+                                             uint32_t w[4]) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(base) + g);
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    const uint64_t p0 = g * 16;
+    if (p0 >= a && p0 + 16 <= b) return;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint64_t wi = (p0 >> 2) + (uint64_t)k;
+        const uint32_t keep = clip_word(0xFFFFFFFFu, wi, a, b);
+        w[k] = (w[k] & keep) | (fill & ~keep);
+    }
+}
+
+// bit 7 of each byte set where the byte satisfies the comparison with t
+__device__ __forceinline__ uint32_t cmp_flags(uint32_t x, int cmp, uint32_t t) {
+    switch (cmp) {
+    case CDC_RS_GEQ: return ge_flags(x, ge_key(t));
+    case CDC_RS_GT: return t >= 255 ? 0u : ge_flags(x, ge_key(t + 1));
+    case CDC_RS_LEQ: return ge_flags(~x, ge_key(255 - t));  // b <= t  <=>  255 - b >= 255 - t
+    case CDC_RS_LT: return t == 0 ? 0u : ge_flags(~x, ge_key(256 - t));
+    default:  // EQ: b >= t and 255 - b >= 255 - t
+        return ge_flags(x, ge_key(t)) & ge_flags(~x, ge_key(255 - t));
+    }
+}
+
+__global__ void k_ebs(int op, const uint8_t* base, uint64_t lo, uint64_t len, const uint64_t* ranges, uint64_t n,
+                      uint8_t* value, uint64_t* pos) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t inv = op == CDC_EBS_MIN ? 0xFFFFFFFFu : 0u;  // the minimum is the complement's maximum
+    for (uint64_t q = warp; q < n; q += nwarps) {
+        uint64_t a = ranges[2 * q], b = ranges[2 * q + 1];
+        if (b > len) b = len;
+        if (a >= b) {
+            if (lane == 0) {
+                value[q] = op == CDC_EBS_MIN ? 255 : 0;
+                if (pos) pos[q] = ranges[2 * q];
+            }
+            continue;
+        }
+        a += lo;
+        b += lo;
+        const uint64_t g0 = a >> 4, g1 = (b - 1) >> 4;
+        ByteMax m;
+        for (uint64_t g = g0 + lane; g <= g1; g += 32) {
+            uint32_t w[4];
+            load_granule(base, g, a, b, inv, w);  // outside bytes read as 0 after the complement
+#pragma unroll
+            for (int k = 0; k < 4; k++) m.add(w[k] ^ inv);
+        }
+        const uint32_t M = __reduce_max_sync(FULLMASK, m.get());
+        uint64_t first = a;  // every byte is the extreme when the maximum is 0
+        if (pos && M > 0) {
+            const uint32_t K = ge_key(M);
+            for (uint64_t g0r = g0; g0r <= g1; g0r += 32) {
+                const uint64_t g = g0r + lane;
+                uint32_t hit = 0xFFFFFFFFu;
+                if (g <= g1) {
+                    uint32_t w[4];
+                    load_granule(base, g, a, b, inv, w);
+#pragma unroll
+                    for (int k = 3; k >= 0; k--) {
+                        const uint32_t f = ge_flags(w[k] ^ inv, K) & clip_word(0xFFFFFFFFu, g * 4 + k, a, b);
+                        if (f) hit = 4u * (uint32_t)k + (uint32_t)((__ffs((int)f) - 1) >> 3);
+                    }
+                }
+                const uint32_t bal = __ballot_sync(FULLMASK, hit != 0xFFFFFFFFu);
+                if (bal) {
+                    const int l = __ffs((int)bal) - 1;
+                    const uint32_t hl = __shfl_sync(FULLMASK, hit, l);
+                    first = (g0r + (uint64_t)l) * 16 + hl;
+                    break;
+                }
+            }
+        }
+        if (lane == 0) {
+            value[q] = (uint8_t)(op == CDC_EBS_MIN ? 255 - M : M);
+            if (pos) pos[q] = first - lo;
+        }
+    }
+}
+
+__global__ void k_rs(int cmp, const uint8_t* base, uint64_t lo, uint64_t len, const uint64_t* ranges,
+                     const uint8_t* thr, uint64_t n, uint64_t* pos) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t q = warp; q < n; q += nwarps) {
+        uint64_t a = ranges[2 * q], b = ranges[2 * q + 1];
+        if (b > len) b = len;
+        const uint64_t end = ranges[2 * q + 1];
+        uint64_t found = end;
+        if (a < b) {
+            const uint32_t t = thr[q];
+            a += lo;
+            b += lo;
+            const uint64_t g0 = a >> 4, g1 = (b - 1) >> 4;
+            for (uint64_t g0r = g0; g0r <= g1; g0r += 32) {
+                const uint64_t g = g0r + lane;
+                uint32_t hit = 0xFFFFFFFFu;
+                if (g <= g1) {
+                    uint32_t w[4];
+                    load_granule(base, g, 0, ~0ull, 0, w);
+#pragma unroll
+                    for (int k = 3; k >= 0; k--) {
+                        const uint32_t f = cmp_flags(w[k], cmp, t) & clip_word(0xFFFFFFFFu, g * 4 + k, a, b);
+                        if (f) hit = 4u * (uint32_t)k + (uint32_t)((__ffs((int)f) - 1) >> 3);
+                    }
+                }
+                const uint32_t bal = __ballot_sync(FULLMASK, hit != 0xFFFFFFFFu);
+                if (bal) {
+                    const int l = __ffs((int)bal) - 1;
+                    const uint32_t hl = __shfl_sync(FULLMASK, hit, l);
+                    found = (g0r + (uint64_t)l) * 16 + hl - lo;
+                    break;
+                }
+            }
+        }
+        if (lane == 0) pos[q] = found;
+    }
+}
+
+int grid_for(uint64_t n) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t warps = (uint64_t)(sms > 0 ? sms : 148) * 64;  // 64 warps of 32 per SM at most
+    const uint64_t w = n < warps ? n : warps;
+    return (int)((w + 7) / 8);  // 8 warps per block
+}
+
+}  // namespace
+}  // namespace cdc
+
+using namespace cdc;
+
+extern "C" cdc_status cdc_ebs(cdc_ebs_op op, const uint8_t* data, size_t len, const uint64_t* d_ranges, size_t n,
+                              uint8_t* d_value, uint64_t* d_pos, cdc_stream stream) {
+    if ((op != CDC_EBS_MAX && op != CDC_EBS_MIN) || (n && (!d_ranges || !d_value)) || (len && !data))
+        return CDC_ERR_INVALID;
+    if (n == 0) return CDC_OK;
+    const uintptr_t p = (uintptr_t)data;
+    const uint8_t* base = (const uint8_t*)(p & ~(uintptr_t)15);
+    k_ebs<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>((int)op, base, p & 15, len, d_ranges, n, d_value, d_pos);
+    return cudaGetLastError() == cudaSuccess ? CDC_OK : CDC_ERR_CUDA;
+}
+
+extern "C" cdc_status cdc_rs(cdc_rs_cmp cmp, const uint8_t* data, size_t len, const uint64_t* d_ranges,
+                             const uint8_t* d_thresholds, size_t n, uint64_t* d_pos, cdc_stream stream) {
+    if ((int)cmp < 0 || (int)cmp > 4 || (n && (!d_ranges || !d_thresholds || !d_pos)) || (len && !data))
+        return CDC_ERR_INVALID;
+    if (n == 0) return CDC_OK;
+    const uintptr_t p = (uintptr_t)data;
+    const uint8_t* base = (const uint8_t*)(p & ~(uintptr_t)15);
+    k_rs<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>((int)cmp, base, p & 15, len, d_ranges, d_thresholds, n,
+                                                        d_pos);
+    return cudaGetLastError() == cudaSuccess ? CDC_OK : CDC_ERR_CUDA;
+}
