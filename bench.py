@@ -391,6 +391,54 @@ def prims_workload(data, dev, n_q: int = 1 << 20, span: int = 8192, reps: int = 
     return out
 
 
+def dedup_workload(dev, base_bytes: int = GIB, n_versions: int = 15, reps: int = 2):
+    """Dedup-shaped versions: a uniform base (seed 2) and 15 versions, each
+    0.1% of its predecessor's bytes edited (seeded insert / delete /
+    overwrite runs of 1..512 bytes), chunked piece by piece (one call per
+    version, device resident) with AE and RAM at 8 KiB mean; then GPU
+    fingerprints and the unique-chunk ratio and space savings (Eq. 1)."""
+    import torch
+
+    import synth
+    from paper_2508_05797_gb300 import Chunker, dedup_report
+
+    vs = synth.versions(2, base_bytes, n_versions)
+    dv = [torch.from_numpy(v).to(dev) for v in vs]
+    total = sum(v.size for v in vs)
+    del vs
+    t = wtable()["uniform_16m_seed0"]
+    res = {"workload": "uniform base of %d MiB (seed 2) + %d versions with 0.1%% edits, %.2f GB, one call per version"
+                       % (base_bytes >> 20, n_versions, total / 1e9)}
+    for alg in ("ae", "ram"):
+        e = t[alg]["8192"]
+        ck = Chunker(dev.index)
+        outs = [torch.empty(d.numel() // e["min"] + 2, dtype=torch.int64, device=dev) for d in dv]
+        cnts = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in dv]
+        for d, o, c in zip(dv, outs, cnts):  # warm-up: workspace sized
+            ck.chunk_async(d, alg, e["w"], e["min"], e["max"], o, c)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            for d, o, c in zip(dv, outs, cnts):
+                ck.chunk_async(d, alg, e["w"], e["min"], e["max"], o, c)
+        e1.record()
+        torch.cuda.synchronize()
+        ck.sync_status()
+        ms = e0.elapsed_time(e1) / reps
+        pieces = [(d, o[:int(c.item())]) for d, o, c in zip(dv, outs, cnts)]
+        rep = dedup_report(pieces)
+        res[alg] = {"GBps": round(total / (ms / 1e3) / 1e9, 1), "ms": round(ms, 2), "chunks": rep["chunks"],
+                    "unique_chunks": rep["unique_chunks"], "unique_ratio": round(rep["unique_chunks"] / rep["chunks"], 5),
+                    "savings_pct": round(100 * rep["savings"], 3), "mean_chunk": round(rep["mean_size"], 1),
+                    "size_quantiles": rep["size_quantiles"]}
+        ck.close()
+        del outs, cnts, pieces
+    del dv
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -436,6 +484,7 @@ def main():
     ap.add_argument("--batched-files", type=int, default=100_000)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-prims", action="store_true", help="skip the EBS / RS measurement")
+    ap.add_argument("--no-dedup", action="store_true", help="skip the dedup-shaped versions measurement")
     ap.add_argument("--streams", type=int, default=3, help="streams the nine calls of a step are spread over")
     ap.add_argument("--ref-sample-mib", type=int, default=32, help="reference arm: bytes per (alg, mean) pair")
     ap.add_argument("--serving-requests", type=int, default=20_000)
@@ -581,6 +630,8 @@ def main():
         line["e2e"] = {"value": round(ncfg * n * e2e_steps * world / dt / 1e9, 2), "unit": "GB/s",
                        "h2d_bytes_per_step": ncfg * n, "d2h_bytes_per_step": int(d2h),
                        "steps": e2e_steps}
+    if rank == 0 and not args.no_dedup:
+        line["dedup"] = dedup_workload(dev)
     if rank == 0 and not args.no_prims:
         line["prims"] = prims_workload(data, dev)
     if rank == 0 and not args.no_serving:

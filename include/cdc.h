@@ -270,6 +270,16 @@ CDC_API cdc_status cdc_ebs(cdc_ebs_op op, const uint8_t* data, size_t len, const
 CDC_API cdc_status cdc_rs(cdc_rs_cmp cmp, const uint8_t* data, size_t len, const uint64_t* d_ranges,
                           const uint8_t* d_thresholds, size_t n, uint64_t* d_pos, cdc_stream stream);
 
+/* 128-bit fingerprints of the chunks of a buffer, for deduplication
+ * reports: chunk i is [d_bounds[i-1], d_bounds[i]) (d_bounds[-1] = 0; the
+ * boundary list cdc_chunk writes, each <= len), its fingerprint d_fp[2i],
+ * d_fp[2i+1]. A non-cryptographic mix of the chunk's bytes and length: equal
+ * chunks give equal fingerprints, different chunks collide with negligible
+ * probability. The paper has no counterpart (it fingerprints on the CPU with
+ * xxHash3, Section 5). Asynchronous on `stream`. */
+CDC_API cdc_status cdc_fingerprint(const uint8_t* data, size_t len, const uint64_t* d_bounds, size_t n,
+                                   uint64_t* d_fp, cdc_stream stream);
+
 /* ---- serving: requests from host memory, continuous batching --------------
  *
  * The paper has no counterpart (it chunks one stream on a CPU). A server owns

@@ -86,6 +86,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
                               ctypes.POINTER(ctypes.c_float), vp], i32),
             "cdc_ebs": ([i32, vp, sz, vp, sz, vp, vp, vp], i32),
             "cdc_rs": ([i32, vp, sz, vp, vp, sz, vp, vp], i32),
+            "cdc_fingerprint": ([vp, sz, vp, sz, vp, vp], i32),
             "cdc_server_create": ([ctypes.POINTER(vp), i32, sz, i32, sz], i32),
             "cdc_server_submit": ([vp, i32, P, vp, sz, vp, sz, u64, ctypes.c_double], i32),
             "cdc_server_poll": ([vp, ctypes.POINTER(Result), i32, ctypes.POINTER(i32), i32], i32),
@@ -104,7 +105,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return ["cdc_create", "cdc_destroy", "cdc_chunk", "cdc_chunk_async", "cdc_chunk_batch", "cdc_chunk_host",
             "cdc_reserve", "cdc_sync_status", "cdc_set_option", "cdc_get_option", "cdc_last_timing",
-            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_ebs", "cdc_rs", "cdc_server_create", "cdc_server_submit",
+            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_ebs", "cdc_rs", "cdc_fingerprint", "cdc_server_create", "cdc_server_submit",
             "cdc_server_poll", "cdc_server_clock", "cdc_server_destroy", "cdc_status_string"]
 
 
@@ -367,6 +368,49 @@ def rs(data, ranges, thresholds, cmp="geq", stream=None):
                                  r.data_ptr() if n else None, t.data_ptr() if n else None, n,
                                  pos.data_ptr() if n else None, _stream_handle(stream)), "cdc_rs")
     return pos
+
+
+def fingerprint(data, bounds, stream=None):
+    """128-bit fingerprints (int64 CUDA tensor of shape (n, 2)) of the chunks
+    of a uint8 CUDA tensor given its boundary list (int64 CUDA tensor)."""
+    import torch
+    assert data.dtype == torch.uint8 and data.is_cuda and data.is_contiguous()
+    b = bounds.contiguous()
+    n = b.numel()
+    fp = torch.empty((n, 2), dtype=torch.int64, device=data.device)
+    _check(load_library().cdc_fingerprint(data.data_ptr() if data.numel() else None, data.numel(),
+                                          b.data_ptr() if n else None, n, fp.data_ptr() if n else None,
+                                          _stream_handle(stream)), "cdc_fingerprint")
+    return fp
+
+
+def dedup_report(pieces):
+    """Deduplication over a list of (uint8 CUDA tensor, its boundaries):
+    chunks are equal when length and fingerprint are (Section 2.2, Eq. 1:
+    space savings = 1 - unique bytes / total bytes). Also the chunk-size
+    distribution (sizes at the 10/50/90/99th percentiles). Sorting and
+    counting use torch on the device."""
+    import torch
+    keys, sizes = [], []
+    for data, b in pieces:
+        if b.numel() == 0:
+            continue
+        fp = fingerprint(data, b)
+        sz = torch.diff(b, prepend=torch.zeros(1, dtype=b.dtype, device=b.device))
+        keys.append(torch.stack([fp[:, 0], fp[:, 1], sz], dim=1))
+        sizes.append(sz)
+    if not keys:
+        return {"chunks": 0, "unique_chunks": 0, "total_bytes": 0, "unique_bytes": 0, "savings": 0.0}
+    k = torch.cat(keys)
+    sz = torch.cat(sizes)
+    uniq, first = torch.unique(k, dim=0, return_inverse=True)
+    total = int(sz.sum().item())
+    ubytes = int(uniq[:, 2].sum().item())
+    q = torch.quantile(sz.double(), torch.tensor([0.1, 0.5, 0.9, 0.99], dtype=torch.float64, device=sz.device))
+    return {"chunks": int(k.shape[0]), "unique_chunks": int(uniq.shape[0]), "total_bytes": total,
+            "unique_bytes": ubytes, "savings": 1.0 - ubytes / max(total, 1),
+            "size_quantiles": {"p10": float(q[0]), "p50": float(q[1]), "p90": float(q[2]), "p99": float(q[3])},
+            "mean_size": total / max(int(k.shape[0]), 1)}
 
 
 STATIC_MAX_LEN = 16 << 20

@@ -182,3 +182,81 @@ extern "C" cdc_status cdc_rs(cdc_rs_cmp cmp, const uint8_t* data, size_t len, co
                                                         d_pos);
     return cudaGetLastError() == cudaSuccess ? CDC_OK : CDC_ERR_CUDA;
 }
+
+// ---- chunk fingerprints ------------------------------------------------------------
+//
+// A 128-bit non-cryptographic fingerprint per chunk, for deduplication
+// reports: two 64-bit multiply-xorshift streams over the chunk's 4-byte words
+// (taken at the chunk's own offsets, the last one zero-padded), each word
+// mixed with its index; lanes of a warp take interleaved words and their
+// states are folded in lane order, then with the length. Equal chunks give
+// equal fingerprints; different chunks collide with negligible probability.
+
+namespace cdc {
+namespace {
+
+__device__ __forceinline__ uint64_t fp_mix(uint64_t x) {
+    x ^= x >> 31;
+    x *= 0x7FB5D329728EA185ull;
+    x ^= x >> 27;
+    x *= 0x81DADEF4BC2DD44Dull;
+    x ^= x >> 33;
+    return x;
+}
+
+// chunk word j: bytes [s + 4j, s + 4j + 4) of the buffer at `base` (4-byte
+// aligned), bytes at or past e read as 0; reads only words holding chunk bytes
+__device__ __forceinline__ uint32_t chunk_word(const uint8_t* base, uint64_t s, uint64_t e, uint64_t j) {
+    const uint64_t p = s + 4 * j;
+    const uint64_t wi = p >> 2;
+    const uint32_t sh = (uint32_t)(p & 3) * 8;
+    const uint32_t* W = reinterpret_cast<const uint32_t*>(base);
+    uint32_t lo = __ldg(W + wi), hi = 0;
+    if (sh && ((wi + 1) << 2) < e) hi = __ldg(W + wi + 1);
+    uint32_t v = sh ? __funnelshift_r(lo, hi, sh) : lo;
+    if (p + 4 > e) v &= 0xFFFFFFFFu >> (8 * (uint32_t)(p + 4 - e));
+    return v;
+}
+
+__global__ void k_fingerprint(const uint8_t* base, uint64_t lo, const uint64_t* bounds, uint64_t n, uint64_t* fp) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t c = warp; c < n; c += nwarps) {
+        const uint64_t s = (c ? bounds[c - 1] : 0) + lo, e = bounds[c] + lo;
+        const uint64_t nw = e > s ? (e - s + 3) / 4 : 0;
+        uint64_t h1 = 0x243F6A8885A308D3ull ^ (uint64_t)lane, h2 = 0x13198A2E03707344ull ^ ((uint64_t)lane << 32);
+        for (uint64_t j = lane; j < nw; j += 32) {
+            const uint64_t x = ((uint64_t)chunk_word(base, s, e, j) << 32) | (uint32_t)j;
+            h1 = fp_mix(h1 ^ x) + 0x9E3779B97F4A7C15ull;
+            h2 = fp_mix(h2 + (x * 0xD6E8FEB86659FD93ull)) ^ (h2 >> 17);
+        }
+        // fold the 32 lane states in lane order (a fixed tree)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t a1 = __shfl_down_sync(0xFFFFFFFFu, h1, o), a2 = __shfl_down_sync(0xFFFFFFFFu, h2, o);
+            if ((lane & (2 * o - 1)) == 0) {
+                h1 = fp_mix(h1 * 0xFF51AFD7ED558CCDull + a1);
+                h2 = fp_mix(h2 ^ (a2 * 0xC4CEB9FE1A85EC53ull));
+            }
+        }
+        if (lane == 0) {
+            const uint64_t L = e - s;
+            fp[2 * c] = fp_mix(h1 ^ L);
+            fp[2 * c + 1] = fp_mix(h2 + L * 0x9E3779B97F4A7C15ull);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace cdc
+
+extern "C" cdc_status cdc_fingerprint(const uint8_t* data, size_t len, const uint64_t* d_bounds, size_t n,
+                                      uint64_t* d_fp, cdc_stream stream) {
+    if ((n && (!d_bounds || !d_fp)) || (len && !data)) return CDC_ERR_INVALID;
+    if (n == 0) return CDC_OK;
+    const uintptr_t p = (uintptr_t)data;
+    const uint8_t* base = (const uint8_t*)(p & ~(uintptr_t)3);
+    k_fingerprint<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(base, p & 3, d_bounds, n, d_fp);
+    return cudaGetLastError() == cudaSuccess ? CDC_OK : CDC_ERR_CUDA;
+}
