@@ -211,7 +211,7 @@ __device__ bool wait_flag_thread(const unsigned int* f, uint32_t epoch, const Ch
 
 // ---- k_spec: speculate and stitch ------------------------------------------------
 
-constexpr int KS = 3;          // per-thread steps per round before the live chains are compacted
+constexpr int KS = 1;          // per-thread steps per round before the live chains are compacted
 
 struct SpecShared {
     unsigned long long ht[HSLOTS];
