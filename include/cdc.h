@@ -218,8 +218,8 @@ CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
  * cdc_chunk_static does what cdc_chunk does, on the CURRENT device, without a
  * handle and without allocating anything: no cudaMalloc / cudaFree, no
  * allocating library routine, no pinned host memory. Its scratch (block
- * summaries, per-segment speculation state and position hashes, control
- * block) is one fixed
+ * summaries, per-segment speculation state, position hashes and step logs,
+ * control block) is one fixed
  * array of CDC_STATIC_SCRATCH_BYTES in the library's device image, so it
  * serves inputs of at most CDC_STATIC_MAX_LEN bytes.
  *
@@ -244,7 +244,7 @@ CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
  *     wrong results. Serialise them.
  */
 #define CDC_STATIC_MAX_LEN ((size_t)16 << 20)
-#define CDC_STATIC_SCRATCH_BYTES ((size_t)10785536)
+#define CDC_STATIC_SCRATCH_BYTES ((size_t)19190528)
 
 CDC_API cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
                                     uint64_t* out_bounds, size_t* n, cdc_stream stream);

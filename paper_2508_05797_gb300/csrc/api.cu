@@ -29,6 +29,8 @@ struct cdc_handle_s {
     size_t groups_cap = 0;      // bytes
     uint8_t* hash = nullptr;    // per-segment position hashes
     size_t hash_cap = 0;        // bytes
+    uint8_t* plog = nullptr;    // per-segment step logs
+    size_t plog_cap = 0;        // bytes
     Ctrl* ctrl = nullptr;
     uint64_t* item_off = nullptr;
     uint64_t* scan_tmp = nullptr;
@@ -127,6 +129,7 @@ extern "C" cdc_status cdc_destroy(cdc_handle h) {
     cudaFree(h->ssup);
     cudaFree(h->groups);
     cudaFree(h->hash);
+    cudaFree(h->plog);
     cudaFree(h->st);
     cudaFree(h->ctrl);
     cudaFree(h->item_off);
@@ -311,6 +314,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     }
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, st)) != CDC_OK) return s;
     if ((s = grow(&h->hash, &h->hash_cap, items * seg_hash_bytes(), false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->plog, &h->plog_cap, items * seg_log_bytes(), false, st)) != CDC_OK) return s;
     if ((s = grow(&h->groups, &h->groups_cap, ((items + GS - 1) / GS + 1) * group_state_bytes(), false, st)) !=
         CDC_OK)
         return s;
@@ -381,6 +385,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     c.d_count = d_count;
     c.st = reinterpret_cast<SegState*>(h->st);
     c.hash = reinterpret_cast<unsigned long long*>(h->hash);
+    c.plog = reinterpret_cast<unsigned long long*>(h->plog);
     c.groups = h->groups;
     c.ctrl = h->ctrl;
     c.timeout_ns = timeout_ns;
@@ -607,6 +612,7 @@ extern "C" cdc_status cdc_reserve(cdc_handle h, cdc_alg alg, cdc_params p, size_
     if (pl.sum != SUM_NONE && (s = grow(&h->ssup, &h->ssup_cap, len / 4096 + 66, false, 0)) != CDC_OK) return s;
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, 0)) != CDC_OK) return s;
     if ((s = grow(&h->hash, &h->hash_cap, items * seg_hash_bytes(), false, 0)) != CDC_OK) return s;
+    if ((s = grow(&h->plog, &h->plog_cap, items * seg_log_bytes(), false, 0)) != CDC_OK) return s;
     if ((s = grow(&h->groups, &h->groups_cap, ((items + GS - 1) / GS + 1) * group_state_bytes(), false, 0)) !=
         CDC_OK)
         return s;
@@ -683,7 +689,7 @@ extern "C" cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream s
 // Same plan, kernels and launch order as run() for a single stream, but every
 // workspace pointer points into g_fixed_scratch, so nothing is allocated.
 // Layout (byte offsets, each part 256-byte aligned):
-//   control block | smax | sarg | ssup | segment states | group states | segment hashes
+//   control block | smax | sarg | ssup | segment states | group states | segment hashes | step logs
 
 namespace {
 constexpr uint64_t round256(uint64_t x) { return (x + 255) & ~255ull; }
@@ -697,6 +703,7 @@ constexpr uint64_t kFixItems = kFixMaxLen / kFixMinSeg + 1;
 constexpr uint64_t kFixSegSlot = 3584;    // >= sizeof(SegState), checked at set-up
 constexpr uint64_t kFixGroupSlot = 2048;  // >= sizeof(GroupState), checked at set-up
 constexpr uint64_t kFixHashSlot = 16384;  // >= a segment's position hash, checked at set-up
+constexpr uint64_t kFixLogSlot = 16384;   // >= a segment's step log, checked at set-up
 constexpr uint64_t kFixGroups = kFixItems / GS + 2;
 constexpr uint64_t kFixCtrlBytes = 512;
 constexpr uint64_t kFixOffSmax = kFixCtrlBytes;
@@ -705,7 +712,8 @@ constexpr uint64_t kFixOffSup = kFixOffSarg + kFixSumBytes;
 constexpr uint64_t kFixOffSt = kFixOffSup + kFixSupBytes;
 constexpr uint64_t kFixOffGroups = kFixOffSt + kFixItems * kFixSegSlot;
 constexpr uint64_t kFixOffHash = kFixOffGroups + kFixGroups * kFixGroupSlot;
-constexpr uint64_t kFixTotal = kFixOffHash + kFixItems * kFixHashSlot;
+constexpr uint64_t kFixOffLog = kFixOffHash + kFixItems * kFixHashSlot;
+constexpr uint64_t kFixTotal = kFixOffLog + kFixItems * kFixLogSlot;
 static_assert(kFixTotal == CDC_STATIC_SCRATCH_BYTES, "scratch layout and header disagree");
 static_assert(sizeof(Ctrl) <= kFixCtrlBytes, "control block does not fit");
 constexpr int kFixMaxDevices = 64;
@@ -723,7 +731,8 @@ static cdc_status fixed_scratch(int dev, cudaStream_t st, uint8_t** out) {
     if (dev < 0 || dev >= kFixMaxDevices) return CDC_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_fixed_mu);
     if (!g_fixed_ptr[dev]) {
-        if (seg_state_bytes() > kFixSegSlot || group_state_bytes() > kFixGroupSlot || seg_hash_bytes() > kFixHashSlot)
+        if (seg_state_bytes() > kFixSegSlot || group_state_bytes() > kFixGroupSlot ||
+            seg_hash_bytes() > kFixHashSlot || seg_log_bytes() > kFixLogSlot)
             return CDC_ERR_INTERNAL;
         uint8_t* p = nullptr;
         if (cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_fixed_scratch) != cudaSuccess || !p) {
@@ -812,6 +821,7 @@ extern "C" cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t*
     c.capacity = *n;
     c.st = reinterpret_cast<SegState*>(scr + kFixOffSt);
     c.hash = reinterpret_cast<unsigned long long*>(scr + kFixOffHash);
+    c.plog = reinterpret_cast<unsigned long long*>(scr + kFixOffLog);
     c.groups = scr + kFixOffGroups;
     c.ctrl = ctrl;
     c.timeout_ns = timeout_ns;

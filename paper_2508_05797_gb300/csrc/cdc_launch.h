@@ -60,6 +60,7 @@ struct ChainLaunch {
     // workspace
     SegState* st;
     unsigned long long* hash;  // per segment: its position hash (seg_hash_bytes())
+    unsigned long long* plog;  // per segment: its step log (seg_log_bytes())
     void* groups;            // GroupState per GS segments
     Ctrl* ctrl;
     uint64_t timeout_ns;
@@ -100,6 +101,7 @@ int chain_smem(int rule, uint32_t win);
 int spec_blocks_per_sm(int rule, uint32_t win);
 size_t seg_state_bytes();
 size_t seg_hash_bytes();
+size_t seg_log_bytes();
 size_t group_state_bytes();
 // ev_spec (may be null) is recorded on `st` right after the speculation kernel
 cudaError_t launch_chain(const ChainLaunch& a, int rule, const ChainGrids& g, cudaStream_t st, int* launches,

@@ -9,25 +9,30 @@
 // they never join at all. The stage therefore splits the input into
 // segments and describes each segment by a transfer table over many chains:
 //
-//  k_spec    (one CTA of NW warps per segment)
+//  k_spec    (one persistent CTA of NW warps per segment at a time)
 //    * Segment bounds: nominal bounds every `seg` bytes are moved forward
 //      out of quiet regions (zero superblocks for RAM/AE, target-less runs
 //      for MAXP), so that every segment starts where chains join quickly.
-//    * Speculate: NL = 32*NW threads each run one chain (per-thread next()
-//      over shared-memory block summaries) from starts spread over the first
-//      `span` bytes; their first KF positions go into a shared-memory hash.
-//    * Stitch: for each distinct exit of the previous segment's NL chains, a
-//      warp follows the chain from that exit until it lands on a hashed
-//      position (or ends on a chain's exit). Result: a table
-//      predecessor chain -> (this segment's chain, boundaries in segment).
+//    * Speculate: NL = 32*NW chains from starts spread over the first `span`
+//      bytes, first one step per thread per round, then (once few are left)
+//      one warp per chain over shared-memory block summaries. Every position a
+//      chain steps from goes into a shared-memory hash (a chain that lands on
+//      a hashed position has joined another and stops), and every step into
+//      the segment's step log.
+//  k_stitch  (after all speculation; no waits): for each distinct exit of the
+//            nearest non-empty predecessor, a warp follows the chain from that
+//            exit until it lands on a hashed position (or ends on a chain's
+//            exit). Result: predecessor chain -> (chain, boundaries in segment).
+//  k_ures    follows the few exits no chain covers into the next segment.
 //  k_compose (one warp per group of GS segments): composes the group's tables.
 //  k_scan    (one warp): carries the true state across the group composites
 //            from the start of the data (the first segment of every file is
 //            exact), settling entries no table covers by following the chain.
 //  k_settle  (one warp per group): carries the state through the group's
 //            segments; records each segment's true entry and global offset.
-//  k_output  (one warp per segment): follows the true chain through the
-//            segment and writes its boundaries at that offset.
+//  k_output  (one warp per segment): replays the true chain from the step log
+//            (the hash names the chain at a position), stepping only where no
+//            record covers it, and writes its boundaries at that offset.
 // Every wait (a segment on its predecessor's speculation) is bounded.
 #include "cdc_device.cuh"
 #include "cdc_launch.h"
@@ -54,7 +59,8 @@ struct __align__(128) SegState {
     unsigned long long unk_exit[NL];  // exit of the followed chain for UNKNOWN entries
     unsigned long long seg_lo, seg_hi, flo, fhi;
     unsigned int geo;                 // bit0 first of file, bit1 last of file, bit2 empty
-    unsigned int flagA;               // X, counts, geometry and hash published
+    unsigned int flagA;               // X, counts, geometry, hash and step log published
+    unsigned int log_n;               // records in the step log (> LOGCAP: it overflowed)
     unsigned int ures_n;              // entries of ures_* below
     // positions that reach this segment off every chain (the nearest non-empty
     // predecessor's uncovered exits), each followed here like a stitch walk
@@ -156,6 +162,26 @@ constexpr int HFILL = 1400;  // stop inserting beyond this many entries
 
 size_t seg_hash_bytes() { return (size_t)HSLOTS * sizeof(unsigned long long); }
 
+// ---- per-segment step log -------------------------------------------------------
+// Every step of every speculative chain of a segment, in the order taken:
+// record = (position | chain << 57, k << 32 | d): the chain visits position,
+// position + d, ..., position + (k - 1) d, and goes on at position + k d.
+// A chain's records appear in increasing position order. The output kernel
+// replays the true chain from these records instead of stepping again.
+constexpr int LOGCAP = 1024;
+size_t seg_log_bytes() { return (size_t)LOGCAP * 16; }
+
+__device__ __forceinline__ void log_step(const ChainLaunch& A, uint64_t item, unsigned int* log_n, uint32_t chain,
+                                         uint64_t pos, uint32_t k, uint64_t d) {
+    const unsigned int i = atomicAdd(log_n, 1u);
+    if (i < (unsigned)LOGCAP) {
+        ulonglong2 r;
+        r.x = pos | ((unsigned long long)chain << 57);
+        r.y = ((unsigned long long)k << 32) | (uint32_t)d;
+        reinterpret_cast<ulonglong2*>(A.plog)[item * (uint64_t)LOGCAP + i] = r;
+    }
+}
+
 __device__ __forceinline__ uint32_t hslot(uint32_t key) { return (key * 2654435761u) >> 21; }  // 11 bits
 constexpr uint32_t H_INSERTED = 0xFFFFFFFFu, H_FULL = 0xFFFFFFFEu;
 
@@ -216,6 +242,7 @@ constexpr int KS = 1;          // per-thread steps per round before the live cha
 struct SpecShared {
     unsigned long long ht[HSLOTS];
     unsigned int fill;
+    unsigned int log_n;            // records in the segment's step log
     unsigned int nq;               // live chains (compacted into threads [0, nq))
     unsigned int nq2;
     unsigned int q_lane[2][NL];    // chain id, position, count of the live chains
@@ -248,7 +275,10 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
             sh.ok = ld_volatile(&A.ctrl->err) == 0;
         }
         for (int i = tid; i < HSLOTS; i += NL) sh.ht[i] = 0ull;
-        if (tid == 0) sh.fill = 0;
+        if (tid == 0) {
+            sh.fill = 0;
+            sh.log_n = 0;
+        }
         __syncthreads();
         const uint64_t item = sh.item;
         if (item >= n_items || !sh.ok) break;
@@ -354,7 +384,9 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                         }
                         uint32_t k;
                         uint64_t dd;
+                        const uint64_t s0 = s;
                         s = advance<RULE>(S, R, P, flo, fhi, s, seg_hi, &k, &dd);
+                        log_step(A, item, &sh.log_n, l, s0, k, dd);
                         c += k;
                         tsteps++;
                         if (s >= seg_hi) {
@@ -419,7 +451,9 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                     }
                     uint32_t k;
                     uint64_t dd;
+                    const uint64_t v0 = v;
                     v = f_advance<RULE>(W, S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+                    if (lane == 0) log_step(A, item, &sh.log_n, l, v0, k, dd);
                     cc += k;
                     if (lane == 0) stat_add(A, STAT_WARP_STEPS, 1);
                 }
@@ -464,6 +498,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
         me->cnt[tid] = c;
         if (tid == 0) {
             me->seg_lo = seg_lo; me->seg_hi = seg_hi; me->flo = flo; me->fhi = fhi; me->geo = geo;
+            me->log_n = sh.log_n;
         }
         // the position hash goes to HBM for the stitch kernels
         if (!first && !empty) {
@@ -995,21 +1030,10 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
         const uint64_t excl = st->excl;
         const uint32_t cnt = st->count;
         const bool first = geo & GEO_FIRST, last = geo & GEO_LAST;
+        // summaries of the segment's window, staged on the first ordinary step
         SumView S{A.smax, A.sarg, dsm, dsm + A.win, 0, 0, A.ssup};
-        if (RULE == RULE_RAM || RULE == RULE_AE || RULE == RULE_MAXP) {
-            uint64_t wb0 = (seg_lo >> 6) & ~15ull;
-            uint64_t wn = A.win;
-            if (wb0 + wn > A.nblk_pad) wn = A.nblk_pad > wb0 ? ((A.nblk_pad - wb0) & ~15ull) : 0;
-            for (uint64_t o = (uint64_t)lane * 16; o < wn; o += 512) {
-                *reinterpret_cast<uint4*>(dsm + o) = *reinterpret_cast<const uint4*>(A.smax + wb0 + o);
-                if (RULE != RULE_MAXP)
-                    *reinterpret_cast<uint4*>(dsm + A.win + o) = *reinterpret_cast<const uint4*>(A.sarg + wb0 + o);
-            }
-            S.wb0 = wb0;
-            S.wn = wn;
-            __syncwarp();
-        }
-        const Win W{dsm, dsm + A.win, S.wb0 << 6, (uint32_t)(S.wn << 6)};
+        Win W{dsm, dsm + A.win, 0, 0};
+        bool staged = !(RULE == RULE_RAM || RULE == RULE_AE || RULE == RULE_MAXP);
         uint64_t v = first ? flo : st->entry_pos;
         uint64_t kb = excl, held = 0;
         uint32_t nb = 0;
@@ -1022,17 +1046,97 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
                 nb = 0;
             }
         };
-        if (!(geo & GEO_EMPTY)) {
-            while (v < seg_hi) {
-                uint32_t k;
-                uint64_t dd;
-                const uint64_t e = f_advance<RULE>(W, S, R, P, flo, fhi, v, seg_hi, &k, &dd);
-                if (lane == 0) stat_add(A, STAT_OUT_STEPS, 1);
-                for (uint32_t i = 0; i < k; i++) {
-                    const uint64_t p = v + i * dd;
-                    if (p != flo) emit(p - flo);
+        // one step the ordinary way (positions not on a logged chain)
+        auto step = [&]() {
+            if (!staged) {
+                uint64_t wb0 = (seg_lo >> 6) & ~15ull;
+                uint64_t wn = A.win;
+                if (wb0 + wn > A.nblk_pad) wn = A.nblk_pad > wb0 ? ((A.nblk_pad - wb0) & ~15ull) : 0;
+                for (uint64_t o = (uint64_t)lane * 16; o < wn; o += 512) {
+                    *reinterpret_cast<uint4*>(dsm + o) = *reinterpret_cast<const uint4*>(A.smax + wb0 + o);
+                    if (RULE != RULE_MAXP)
+                        *reinterpret_cast<uint4*>(dsm + A.win + o) =
+                            *reinterpret_cast<const uint4*>(A.sarg + wb0 + o);
                 }
-                v = e;
+                S.wb0 = wb0;
+                S.wn = wn;
+                W.p0 = wb0 << 6;
+                W.nb = (uint32_t)(wn << 6);
+                staged = true;
+                __syncwarp();
+            }
+            uint32_t k;
+            uint64_t dd;
+            const uint64_t e = f_advance<RULE>(W, S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+            if (lane == 0) stat_add(A, STAT_OUT_STEPS, 1);
+            for (uint32_t i = 0; i < k; i++) {
+                const uint64_t p = v + i * dd;
+                if (p != flo) emit(p - flo);
+            }
+            v = e;
+        };
+        if (!(geo & GEO_EMPTY)) {
+            const uint32_t ln = st->log_n;
+            const bool use_log = ln <= (uint32_t)LOGCAP;
+            const unsigned long long* ht = A.hash + item * (uint64_t)HSLOTS;
+            const ulonglong2* lg = reinterpret_cast<const ulonglong2*>(A.plog) + item * (uint64_t)LOGCAP;
+            constexpr uint64_t POS = (1ull << 57) - 1;
+            while (v < seg_hi) {
+                // the chain whose recorded path holds v (the first segment of a
+                // file: chain 0 from the file start; it is never hashed)
+                int m = -1;
+                if (use_log) {
+                    if (first) {
+                        m = v == flo ? 0 : -1;
+                    } else {
+                        const uint32_t hv = hfind(ht, (uint32_t)(v - seg_lo) + 1u);
+                        m = hv == ~0u ? -1 : (int)(hv >> 16);
+                    }
+                }
+                if (m < 0) {
+                    step();
+                    continue;
+                }
+                // replay chain m's records from v on, in log order (= path order)
+                const uint64_t v_start = v;
+                bool broken = false;
+                for (uint32_t b0 = 0; b0 < ln && !broken; b0 += 128) {
+                    ulonglong2 r[4];
+                    bool mine[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const uint32_t i = b0 + 32 * u + (uint32_t)lane;
+                        mine[u] = false;
+                        if (i < ln) {
+                            r[u] = lg[i];
+                            mine[u] = (uint32_t)(r[u].x >> 57) == (uint32_t)m && (r[u].x & POS) >= v_start;
+                        } else {
+                            r[u] = make_ulonglong2(0, 0);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        uint32_t bal = __ballot_sync(FULL, mine[u]);
+                        while (bal && !broken) {
+                            const int src = __ffs((int)bal) - 1;
+                            bal &= bal - 1;
+                            const uint64_t p = __shfl_sync(FULL, r[u].x, src) & POS;
+                            const uint64_t kd = __shfl_sync(FULL, r[u].y, src);
+                            if (p != v) {  // not the continuation of the path: leave it to ordinary steps
+                                broken = true;
+                                break;
+                            }
+                            const uint32_t k = (uint32_t)(kd >> 32);
+                            const uint64_t d = (uint32_t)kd;
+                            for (uint32_t i = 0; i < k; i++) {
+                                const uint64_t q = p + i * d;
+                                if (q != flo) emit(q - flo);
+                            }
+                            v = p + (uint64_t)k * d;
+                        }
+                    }
+                }
+                if (v == v_start) step();  // no record continued the path
             }
             if (last) emit(fhi - flo);
         }
