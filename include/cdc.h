@@ -202,8 +202,9 @@ CDC_API cdc_status cdc_profile_collect(cdc_handle h, int* calls, double* summary
  * resolution, output steps, empty segments, chains handed to whole warps,
  * then clock cycles summed over segments (set-up, speculation, merge
  * resolution, stitching), per-thread rounds, the cycles of the rounds and of
- * the one-warp-per-chain phase, stitch walks of more than 64 steps, and
- * (steps << 32 | segment) of the longest one (21 counters).
+ * the one-warp-per-chain phase, stitch walks of more than 64 steps,
+ * (steps << 32 | segment) of the longest one, the output kernel's passes over
+ * step logs, records it replayed and its cycles (24 counters).
  * Synchronises `stream`. */
 CDC_API cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream stream);
 
@@ -279,6 +280,57 @@ CDC_API cdc_status cdc_rs(cdc_rs_cmp cmp, const uint8_t* data, size_t len, const
  * xxHash3, Section 5). Asynchronous on `stream`. */
 CDC_API cdc_status cdc_fingerprint(const uint8_t* data, size_t len, const uint64_t* d_bounds, size_t n,
                                    uint64_t* d_fp, cdc_stream stream);
+
+/* ---- resumable chunking of a stream that arrives in pieces ----------------
+ *
+ * A feed chunks one stream that is handed over piece by piece (device
+ * buffers of any size, including 0) and emits each chunk as soon as no later
+ * byte can change it. Each algorithm works one chunk at a time (Section 3.3),
+ * and the chunk that starts at s depends only on the bytes before s + H, with
+ * H = max for RAM / AE (the forced cut, Section 2.1) and H = max + w for MAXP
+ * (a target's right window, Section 2.1; MAXP also reads the w bytes before s,
+ * which the feed keeps). So a push emits every chunk whose start s has
+ * s + H <= bytes received, and the final push emits the rest, ending at the
+ * stream's length. The emitted lists of all pushes, concatenated, equal
+ * cdc_chunk of the whole stream.
+ *
+ * The feed keeps the bytes from the first unsettled start (less w for MAXP)
+ * in a device staging buffer it owns (at most H + w bytes between pushes)
+ * and copies each piece behind them; it runs the chain on the handle h, which
+ * it borrows (h must outlive the feed; calls on h and on the feed must not
+ * overlap). Staging grows with the largest piece (cudaMalloc outside any
+ * capture); a feed cannot be captured into a CUDA graph.
+ */
+typedef struct cdc_feed_s* cdc_feed;
+
+/* Create a feed for one stream on the current device, chunked with alg and p
+ * (the parameter rules of cdc_chunk). Nothing is staged until the first push. */
+CDC_API cdc_status cdc_feed_create(cdc_feed* out, cdc_handle h, cdc_alg alg, cdc_params p);
+
+/* Append `len` bytes of device memory at `piece` (the stream's next bytes)
+ * and write the newly settled boundaries to out_bounds (device, uint64,
+ * offsets from the START OF THE STREAM, increasing). *n: on entry the
+ * capacity of out_bounds in elements, on return the count written. final_piece
+ * != 0 marks the end of the stream (the last boundary is then the total
+ * length); a push after it is CDC_ERR_INVALID. On CDC_ERR_CAPACITY *n holds
+ * the count needed, nothing is consumed and the piece stays staged: push
+ * again with len 0 (and the same final_piece) and a larger buffer.
+ * Synchronises `stream` once; `piece` may be reused when the call returns.
+ * Consecutive pushes may use different streams (the feed orders its own
+ * copies with an event). */
+CDC_API cdc_status cdc_feed_push(cdc_feed f, const uint8_t* piece, size_t len, int final_piece,
+                                 uint64_t* out_bounds, size_t* n, cdc_stream stream);
+
+/* Bytes received so far and the stream offset where the next (unsettled)
+ * chunk starts; either pointer may be NULL. */
+CDC_API cdc_status cdc_feed_position(cdc_feed f, uint64_t* received, uint64_t* next_start);
+
+/* Start a new stream on the same feed (same algorithm and parameters),
+ * keeping its buffers. */
+CDC_API cdc_status cdc_feed_reset(cdc_feed f);
+
+/* Release the feed's staging buffers (not the handle). NULL is accepted. */
+CDC_API cdc_status cdc_feed_destroy(cdc_feed f);
 
 /* ---- serving: requests from host memory, continuous batching --------------
  *

@@ -116,6 +116,35 @@ class Oracle:
         arr = self._buf(data)
         return int(self.lib.oracle_rs(RS_CMPS[cmp], arr.ctypes.data if arr.size else None, arr.size, a, b, t))
 
+    def horizon(self, alg, w: int, mx: int) -> int:
+        """Bytes after a chunk start s that decide the chunk from s: RAM and AE
+        never look at or past s + max (the forced cut, Section 2.1); a MAXP
+        target also needs its w right neighbours (Section 2.1), so max + w."""
+        return mx + (w if alg_id(alg) == MAXP else 0)
+
+    def chunk_pieces(self, alg, pieces, w: int, mn: int, mx: int, horizon: int | None = None) -> list:
+        """The stream chunked while it arrives piece by piece (the last piece
+        ends it). For each piece: the chunk ends (offsets from the stream
+        start) that the bytes received so far settle, i.e. those of the
+        chunks whose start s has s + horizon <= bytes received; the last
+        piece adds the rest, up to the stream's length. Each chunk is one step
+        s -> next(s) of the sequential loop (Section 3.3) over the bytes
+        received so far. `horizon` overrides the rule's horizon (tests plant
+        a wrong one)."""
+        H = self.horizon(alg, w, mx) if horizon is None else horizon
+        buf = np.zeros(0, dtype=np.uint8)
+        s, out = 0, []
+        for i, piece in enumerate(pieces):
+            buf = np.concatenate([buf, self._buf(piece)])
+            L = buf.size
+            final = i == len(pieces) - 1
+            ends = []
+            while s < L and (final or s + H <= L):
+                s = self.next(alg, buf, s, w, mn, mx)
+                ends.append(s)
+            out.append(np.array(ends, dtype=np.uint64))
+        return out
+
 
 EBS_OPS = {"max": 0, "min": 1}
 RS_CMPS = {"gt": 0, "lt": 1, "geq": 2, "leq": 3, "eq": 4}
@@ -146,3 +175,7 @@ def next_cut(alg, data, s: int, w: int, mn: int, mx: int) -> int:
 
 def maxp_targets(data, w: int) -> np.ndarray:
     return get().maxp_targets(data, w)
+
+
+def chunk_pieces(alg, pieces, w: int, mn: int, mx: int, horizon: int | None = None) -> list:
+    return get().chunk_pieces(alg, pieces, w, mn, mx, horizon)

@@ -19,7 +19,8 @@ OPT_STATS = 6
 OPT_WARP_CHAINS = 7
 STAT_NAMES = ["segments", "thread_steps", "warp_steps", "merges", "stitch_walks", "stitch_steps", "unknown",
               "hash_full", "scan_follows", "out_steps", "empty", "survivors", "cyc_setup", "cyc_threads",
-              "cyc_warps", "cyc_stitch", "rounds", "cyc_rounds", "cyc_surv", "stitch_long", "stitch_maxw"]
+              "cyc_warps", "cyc_stitch", "rounds", "cyc_rounds", "cyc_surv", "stitch_long", "stitch_maxw",
+              "out_passes", "out_recs", "cyc_output"]
 STATUS = ["CDC_OK", "CDC_ERR_INVALID", "CDC_ERR_CAPACITY", "CDC_ERR_CUDA", "CDC_ERR_TIMEOUT",
           "CDC_ERR_NOMEM", "CDC_ERR_INTERNAL"]
 OK, ERR_INVALID, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_INTERNAL = range(7)
@@ -87,6 +88,11 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "cdc_ebs": ([i32, vp, sz, vp, sz, vp, vp, vp], i32),
             "cdc_rs": ([i32, vp, sz, vp, vp, sz, vp, vp], i32),
             "cdc_fingerprint": ([vp, sz, vp, sz, vp, vp], i32),
+            "cdc_feed_create": ([ctypes.POINTER(vp), vp, i32, P], i32),
+            "cdc_feed_push": ([vp, vp, sz, i32, vp, ctypes.POINTER(sz), vp], i32),
+            "cdc_feed_position": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64)], i32),
+            "cdc_feed_reset": ([vp], i32),
+            "cdc_feed_destroy": ([vp], i32),
             "cdc_server_create": ([ctypes.POINTER(vp), i32, sz, i32, sz], i32),
             "cdc_server_submit": ([vp, i32, P, vp, sz, vp, sz, u64, ctypes.c_double], i32),
             "cdc_server_poll": ([vp, ctypes.POINTER(Result), i32, ctypes.POINTER(i32), i32], i32),
@@ -105,7 +111,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return ["cdc_create", "cdc_destroy", "cdc_chunk", "cdc_chunk_async", "cdc_chunk_batch", "cdc_chunk_host",
             "cdc_reserve", "cdc_sync_status", "cdc_set_option", "cdc_get_option", "cdc_last_timing",
-            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_ebs", "cdc_rs", "cdc_fingerprint", "cdc_server_create", "cdc_server_submit",
+            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_ebs", "cdc_rs", "cdc_fingerprint", "cdc_feed_create", "cdc_feed_push",
+            "cdc_feed_position", "cdc_feed_reset", "cdc_feed_destroy", "cdc_server_create", "cdc_server_submit",
             "cdc_server_poll", "cdc_server_clock", "cdc_server_destroy", "cdc_status_string"]
 
 
@@ -264,6 +271,59 @@ class Chunker:
 
     def sync_status(self, stream=None):
         _check(self.lib.cdc_sync_status(self.h, _stream_handle(stream)), "device-side status")
+
+
+class Feed:
+    """cdc_feed: resumable chunking of one stream handed over in pieces.
+    push() returns the boundaries settled by that piece (offsets from the start
+    of the stream); concatenated over all pushes they equal chunk() of the
+    whole stream. Borrows the Chunker's handle."""
+
+    def __init__(self, chunker: Chunker, alg, w: int, mn: int, mx: int):
+        self.lib = chunker.lib
+        self.chunker = chunker
+        self.mn = mn
+        self.horizon = mx + (w if alg_id(alg) == ALGS["maxp"] else 0)
+        h = ctypes.c_void_p()
+        _check(self.lib.cdc_feed_create(ctypes.byref(h), chunker.h, alg_id(alg), Params(w, mn, mx)),
+               "cdc_feed_create")
+        self.f = h
+
+    def position(self):
+        """(bytes received, stream offset of the next unsettled chunk start)"""
+        r, s = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self.lib.cdc_feed_position(self.f, ctypes.byref(r), ctypes.byref(s)), "cdc_feed_position")
+        return r.value, s.value
+
+    def push(self, piece, final: bool = False, out=None, stream=None):
+        import torch
+        n = 0 if piece is None else piece.numel()
+        if piece is not None:
+            assert piece.dtype == torch.uint8 and piece.is_cuda and piece.is_contiguous()
+        received, start = self.position()
+        if out is None:
+            out = torch.empty(max_boundaries(received + n - start, self.mn) + 1, dtype=torch.int64,
+                              device=torch.device("cuda", self.chunker.device))
+        cap = ctypes.c_size_t(out.numel())
+        st = self.lib.cdc_feed_push(self.f, piece.data_ptr() if n else None, n, 1 if final else 0,
+                                    out.data_ptr(), ctypes.byref(cap), _stream_handle(stream))
+        _check(st, "cdc_feed_push (count %d)" % cap.value)
+        return out[:cap.value]
+
+    def reset(self):
+        """Start a new stream, keeping the feed's device buffers."""
+        _check(self.lib.cdc_feed_reset(self.f), "cdc_feed_reset")
+
+    def close(self):
+        if self.f:
+            self.lib.cdc_feed_destroy(self.f)
+            self.f = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -298,10 +298,11 @@ static Geo geometry(const uint8_t* data, uint64_t len) {
 // launch the summary and chain stages; n_files == 0 means one stream
 static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data, uint64_t len,
                       const uint64_t* d_file_off, uint64_t n_files, uint64_t* out, uint64_t capacity,
-                      uint64_t* bounds_index, uint64_t* d_count, cudaStream_t st) {
+                      uint64_t* bounds_index, uint64_t* d_count, cudaStream_t st, uint64_t ctx = 0) {
     cudaSetDevice(h->device);
     const Plan pl = make_plan(h, alg, p);
-    const Geo g = geometry(data, len);
+    // summaries cover the context bytes before data too (ctx > 0: one stream only)
+    const Geo g = geometry(data - ctx, len + ctx);
     const bool batch = d_file_off != nullptr;
     const uint64_t seg = pick_seg(h, len, batch ? n_files : 1);
     const uint64_t items = batch ? len / seg + n_files + 1 : (len + seg - 1) / seg;
@@ -361,8 +362,9 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     ChainLaunch c;
     memset(&c, 0, sizeof c);
     c.base = g.base;
-    c.lo = g.lo;
+    c.lo = g.lo + ctx;
     c.hi = g.hi;
+    c.wctx = ctx;
     c.smax = h->smax;
     c.sarg = h->sarg ? h->sarg : h->smax;
     c.ssup = h->ssup;
@@ -455,6 +457,14 @@ extern "C" cdc_status cdc_chunk(cdc_handle h, cdc_alg alg, cdc_params p, const u
     *n = (size_t)total;
     return total > cap ? CDC_ERR_CAPACITY : CDC_OK;
 }
+
+cdc_status cdc::chunk_in_context(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data, uint64_t len,
+                                 uint64_t ctx, uint64_t* out, uint64_t capacity, uint64_t* d_count,
+                                 cudaStream_t st) {
+    return run(h, alg, p, data, len, nullptr, 0, out, capacity, nullptr, d_count, st, ctx);
+}
+
+cdc_status cdc::handle_status(cdc_handle h, cudaStream_t st) { return collect(h, st, nullptr); }
 
 extern "C" cdc_status cdc_chunk_async(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
                                       uint64_t* out_bounds, size_t capacity, uint64_t* d_count,

@@ -20,7 +20,7 @@ struct Ctrl {
     unsigned int err;            // sticky error bits, cleared by the host
     unsigned int stats_on;       // 1: kernels accumulate the counters below
     unsigned int pad[5];
-    unsigned long long stats[21];  // see STAT_* (reset by the host)
+    unsigned long long stats[24];  // see STAT_* (reset by the host)
 };
 enum : int {
     STAT_SEGMENTS = 0,      // non-empty segments speculated
@@ -44,7 +44,10 @@ enum : int {
     STAT_CYC_SURV = 18,     // cycles of the one-warp-per-chain phase (part of STAT_CYC_THREADS)
     STAT_STITCH_LONG = 19,  // stitch walks of more than 64 steps
     STAT_STITCH_MAXW = 20,  // (steps << 32) | segment of the longest stitch walk
-    STAT_N = 21
+    STAT_OUT_PASSES = 21,   // passes of the output kernel over a step log
+    STAT_OUT_RECS = 22,     // step-log records the output kernel replayed
+    STAT_CYC_OUTPUT = 23,   // cycles of the output kernel, summed over segments
+    STAT_N = 24
 };
 enum : unsigned int { ERR_TIMEOUT = 1u, ERR_INTERNAL = 2u };
 

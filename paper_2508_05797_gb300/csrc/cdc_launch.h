@@ -40,6 +40,9 @@ struct ChainLaunch {
     // file_off (logical offsets), with item_off / item_file from the batch set-up
     const uint64_t* file_off;
     uint64_t single_len;
+    // one stream only: bytes before its start that belong to the same data
+    // (a resumed stream); MAXP windows may reach into them, chains start at lo
+    uint64_t wctx;
     uint64_t n_files;
     const uint64_t* item_off;
     const uint32_t* item_file;
@@ -112,5 +115,19 @@ cudaError_t launch_batch_setup(const uint64_t* file_off, uint64_t n_files, uint6
                                uint32_t* item_file, uint64_t* scan_tmp, Ctrl* ctrl, cudaStream_t st,
                                int* launches);
 uint64_t batch_scan_tmp_elems(uint64_t n_files);
+
+}  // namespace cdc
+
+#include "../../include/cdc.h"
+
+namespace cdc {
+
+// cdc_chunk_async of [data, data + len) whose `ctx` bytes before `data` belong
+// to the same stream: the chain starts at data, MAXP windows may read the
+// context. The count (boundaries are offsets from data) goes to *d_count.
+cdc_status chunk_in_context(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data, uint64_t len,
+                            uint64_t ctx, uint64_t* out, uint64_t capacity, uint64_t* d_count, cudaStream_t st);
+// Synchronise st and report (and clear) the handle's device-side errors.
+cdc_status handle_status(cdc_handle h, cudaStream_t st);
 
 }  // namespace cdc

@@ -94,41 +94,75 @@ constexpr uint32_t UNRESOLVED = 0xFFFEu;  // composite entry not computable with
 
 struct Geo {
     uint64_t flo, fhi, seg_lo, seg_hi, f;
-    bool first, last, empty;
+    bool first;
 };
 
 // Move a nominal bound x forward to the first 4 KiB-aligned y whose
 // neighbourhood [y - before, y + after) meets no quiet run (a run of at least
 // `quiet_run` consecutive quiet superblocks, counted over the whole file).
 // The rule depends on y alone, so the result is monotone in x and adjacent
-// segments stay contiguous. Single forward pass.
-__device__ uint64_t adjust_bound(const ChainLaunch& A, uint64_t x, uint64_t flo, uint64_t fhi) {
+// segments stay contiguous. One forward pass over the superblocks, taken 32
+// at a time by the calling warp (every lane returns the same bound): the
+// superblock summaries of a batch are loaded at once, and the events of the
+// pass -- the window end reached, a quiet run long enough to push y -- are
+// found with ballots in the order a single thread would meet them.
+__device__ uint64_t adjust_bound(const ChainLaunch& A, uint64_t x, uint64_t flo, uint64_t fhi, int lane) {
     if (A.quiet_run == 0 || x <= flo) return x <= flo ? flo : x;
     if (x >= fhi) return fhi;
     const uint64_t cap = x + A.adj_cap;
     const uint64_t qf = flo >> 12;
+    const uint32_t QR = A.quiet_run;
     uint64_t y = x;
     uint64_t q = (y > flo + A.adj_before ? y - A.adj_before : flo) >> 12;
-    // length of the quiet run that ends just before q
+    // length of the quiet run that ends just before q (counted up to QR)
     uint32_t run = 0;
-    for (uint64_t r = q; r > qf && run < A.quiet_run && A.ssup[r - 1] == 0; r--) run++;
-    for (;;) {
-        const uint64_t qpos = q << 12;
-        if (qpos >= y + A.adj_after || qpos >= fhi) return y;  // clean window found
-        const bool quiet = A.ssup[q] == 0;
-        run = quiet ? run + 1 : 0;
-        if (run >= A.quiet_run) {
-            uint64_t ny = ((q + 1) << 12) + A.adj_before;
+    for (uint64_t r0 = q; run < QR;) {
+        const bool qt = r0 > qf + (uint64_t)lane && A.ssup[r0 - 1 - lane] == 0;
+        const uint32_t m = __ballot_sync(FULL, qt);
+        const uint32_t t = m == FULL ? 32u : (uint32_t)(__ffs((int)~m) - 1);
+        run += t;
+        if (t < 32) break;
+        r0 -= 32;
+    }
+    if (run > QR) run = QR;
+    const uint32_t upto = lane == 31 ? FULL : ((2u << lane) - 1);  // lanes 0..lane
+    for (;; q += 32) {
+        const uint64_t qq = q + (uint64_t)lane;
+        const bool valid = (qq << 12) < fhi;
+        const uint32_t qm = __ballot_sync(FULL, valid && A.ssup[qq] == 0);
+        uint32_t i = 0;  // batch positions before i are done
+        for (;;) {
+            const uint32_t from = ~0u << i;
+            // the window end, checked first at every position (with the current y)
+            const uint32_t tmask = __ballot_sync(FULL, !valid || (qq << 12) >= y + A.adj_after) & from;
+            // quiet run ending at each position from i on
+            const uint32_t zeros = ~qm & upto & from;
+            const uint32_t rj = zeros ? (uint32_t)lane - (31u - (uint32_t)__clz((int)zeros))
+                                      : run + (uint32_t)lane - i + 1u;
+            const uint32_t gmask = __ballot_sync(FULL, ((qm >> lane) & 1u) && rj >= QR) & from;
+            const int ft = tmask ? __ffs((int)tmask) - 1 : 32;
+            const int fg = gmask ? __ffs((int)gmask) - 1 : 32;
+            if (ft <= fg) {
+                if (ft < 32) return y;
+                run = __shfl_sync(FULL, rj, 31);  // no event left in this batch
+                break;
+            }
+            uint64_t ny = ((q + (uint64_t)fg + 1) << 12) + A.adj_before;
             ny = (ny + 4095) & ~4095ull;
             if (ny > y) y = ny;
             if (y >= fhi) return fhi;
             if (y >= cap) return cap < fhi ? cap : fhi;
+            run = __shfl_sync(FULL, rj, fg);
+            i = (uint32_t)fg + 1;
+            if (i == 32) break;
         }
-        q++;
     }
 }
 
-__device__ Geo seg_geo(const ChainLaunch& A, uint64_t item) {
+// Geometry of segment `item`; seg_lo and seg_hi as adjust_bound() gives them.
+// Called by whole warps; `bound` selects which bound the warp computes
+// (0: seg_lo, 1: seg_hi, 2: both).
+__device__ Geo seg_geo(const ChainLaunch& A, uint64_t item, int lane, int bound) {
     Geo g;
     uint64_t flo_l, fhi_l, kin;
     if (A.file_off == nullptr) {
@@ -143,11 +177,9 @@ __device__ Geo seg_geo(const ChainLaunch& A, uint64_t item) {
     g.fhi = A.lo + fhi_l;
     const uint64_t nlo = g.flo + kin * A.seg, nhi = nlo + A.seg;
     g.first = kin == 0;
-    g.seg_lo = g.first ? g.flo : adjust_bound(A, nlo, g.flo, g.fhi);
-    g.seg_hi = nhi >= g.fhi ? g.fhi : adjust_bound(A, nhi, g.flo, g.fhi);
-    if (g.seg_hi < g.seg_lo) g.seg_hi = g.seg_lo;
-    g.empty = g.seg_hi == g.seg_lo;
-    g.last = !g.empty && g.seg_hi == g.fhi;
+    g.seg_lo = g.seg_hi = 0;
+    if (bound != 1) g.seg_lo = g.first ? g.flo : adjust_bound(A, nlo, g.flo, g.fhi, lane);
+    if (bound != 0) g.seg_hi = nhi >= g.fhi ? g.fhi : adjust_bound(A, nhi, g.flo, g.fhi, lane);
     return g;
 }
 
@@ -282,10 +314,19 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
         __syncthreads();
         const uint64_t item = sh.item;
         if (item >= n_items || !sh.ok) break;
-        if (tid == 0) {
-            Geo g = seg_geo(A, item);
-            sh.geo[0] = g.seg_lo; sh.geo[1] = g.seg_hi; sh.geo[2] = g.flo; sh.geo[3] = g.fhi;
-            sh.geo[4] = (g.first ? GEO_FIRST : 0u) | (g.last ? GEO_LAST : 0u) | (g.empty ? GEO_EMPTY : 0u);
+        if (tid < 64) {  // warp 0: seg_lo, warp 1: seg_hi
+            const Geo g = seg_geo(A, item, lane, tid >> 5);
+            if (tid == 0) {
+                sh.geo[0] = g.seg_lo; sh.geo[2] = g.flo; sh.geo[3] = g.fhi;
+                sh.geo[4] = g.first ? GEO_FIRST : 0u;
+            }
+            if (tid == 32) sh.geo[1] = g.seg_hi;
+        }
+        __syncthreads();
+        if (tid == 0) {  // empty: the bounds met (a quiet run pushed both); last: it ends the file
+            if (sh.geo[1] < sh.geo[0]) sh.geo[1] = sh.geo[0];
+            const bool empty = sh.geo[1] == sh.geo[0];
+            sh.geo[4] |= (empty ? GEO_EMPTY : 0u) | (!empty && sh.geo[1] == sh.geo[3] ? GEO_LAST : 0u);
         }
         __syncthreads();
         const uint64_t seg_lo = sh.geo[0], seg_hi = sh.geo[1], flo = sh.geo[2], fhi = sh.geo[3];
@@ -385,7 +426,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                         uint32_t k;
                         uint64_t dd;
                         const uint64_t s0 = s;
-                        s = advance<RULE>(S, R, P, flo, fhi, s, seg_hi, &k, &dd);
+                        s = advance<RULE>(S, R, P, flo - A.wctx, fhi, s, seg_hi, &k, &dd);
                         log_step(A, item, &sh.log_n, l, s0, k, dd);
                         c += k;
                         tsteps++;
@@ -452,7 +493,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                     uint32_t k;
                     uint64_t dd;
                     const uint64_t v0 = v;
-                    v = f_advance<RULE>(W, S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+                    v = f_advance<RULE>(W, S, R, P, flo - A.wctx, fhi, v, seg_hi, &k, &dd);
                     if (lane == 0) log_step(A, item, &sh.log_n, l, v0, k, dd);
                     cc += k;
                     if (lane == 0) stat_add(A, STAT_WARP_STEPS, 1);
@@ -533,7 +574,7 @@ __device__ __forceinline__ uint64_t nonempty_pred(const ChainLaunch& A, uint64_t
 template <int RULE>
 __device__ uint32_t stitch_walk(const ChainLaunch& A, const SumView& S, const RawView& R, const Prm& P,
                                 const unsigned long long* ht, const unsigned long long* X, const unsigned int* cnt,
-                                uint64_t seg_lo, uint64_t seg_hi, uint64_t flo, uint64_t fhi, bool last, uint64_t e,
+                                uint64_t seg_lo, uint64_t seg_hi, uint64_t wflo, uint64_t fhi, bool last, uint64_t e,
                                 uint64_t* ux, uint64_t item) {
     const int lane = threadIdx.x & 31;
     uint32_t nsteps = 0;
@@ -548,7 +589,7 @@ __device__ uint32_t stitch_walk(const ChainLaunch& A, const SumView& S, const Ra
         }
         uint32_t k;
         uint64_t dd;
-        v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+        v = w_advance<RULE>(S, R, P, wflo, fhi, v, seg_hi, &k, &dd);
         ne += k;
         nsteps++;
         if (lane == 0) stat_add(A, STAT_STITCH_STEPS, 1);
@@ -639,7 +680,7 @@ __global__ void __launch_bounds__(NL) k_stitch(ChainLaunch A) {
                 const uint64_t e = __shfl_sync(FULL, xp, ld);
                 const uint32_t same = __ballot_sync(FULL, xp == e) & todo;
                 uint64_t ux;
-                const uint32_t res = stitch_walk<RULE>(A, S, R, P, sh.ht, sh.X, sh.cnt, seg_lo, seg_hi, flo, fhi,
+                const uint32_t res = stitch_walk<RULE>(A, S, R, P, sh.ht, sh.X, sh.cnt, seg_lo, seg_hi, flo - A.wctx, fhi,
                                                        last, e, &ux, item);
                 if ((same >> lane) & 1u) {
                     tab = res;
@@ -711,7 +752,7 @@ __global__ void __launch_bounds__(NL) k_ures(ChainLaunch A) {
                         if (up[jj] == e) up[jj] = ~0ull;
                     todo = __ballot_sync(FULL, up[j] != ~0ull);
                     uint64_t ux;
-                    const uint32_t res = stitch_walk<RULE>(A, S, R, P, sh.ht, sh.X, sh.cnt, seg_lo, seg_hi, flo, fhi,
+                    const uint32_t res = stitch_walk<RULE>(A, S, R, P, sh.ht, sh.X, sh.cnt, seg_lo, seg_hi, flo - A.wctx, fhi,
                                                            last, e, &ux, item);
                     if (lane == 0) {
                         me->ures_pos[nu] = e;
@@ -737,13 +778,13 @@ __device__ uint32_t follow(const ChainLaunch& A, const SegState* st, uint64_t v,
     const SumView S{A.smax, A.sarg, nullptr, nullptr, 0, 0, A.ssup};
     const RawView R{A.base, A.inv};
     const Prm P{A.w, A.mn, A.mx};
-    const uint64_t seg_hi = st->seg_hi, flo = st->flo, fhi = st->fhi;
+    const uint64_t seg_hi = st->seg_hi, wflo = st->flo - A.wctx, fhi = st->fhi;
     const bool last = st->geo & GEO_LAST;
     uint32_t n = 0;
     while (v < seg_hi) {
         uint32_t k;
         uint64_t dd;
-        v = w_advance<RULE>(S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+        v = w_advance<RULE>(S, R, P, wflo, fhi, v, seg_hi, &k, &dd);
         n += k;
     }
     if (last) n++;
@@ -1067,7 +1108,7 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
             }
             uint32_t k;
             uint64_t dd;
-            const uint64_t e = f_advance<RULE>(W, S, R, P, flo, fhi, v, seg_hi, &k, &dd);
+            const uint64_t e = f_advance<RULE>(W, S, R, P, flo - A.wctx, fhi, v, seg_hi, &k, &dd);
             if (lane == 0) stat_add(A, STAT_OUT_STEPS, 1);
             for (uint32_t i = 0; i < k; i++) {
                 const uint64_t p = v + i * dd;
@@ -1075,6 +1116,7 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
             }
             v = e;
         };
+        const long long t_seg = clock64();
         if (!(geo & GEO_EMPTY)) {
             const uint32_t ln = st->log_n;
             const bool use_log = ln <= (uint32_t)LOGCAP;
@@ -1100,6 +1142,7 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
                 // replay chain m's records from v on, in log order (= path order)
                 const uint64_t v_start = v;
                 bool broken = false;
+                if (lane == 0) stat_add(A, STAT_OUT_PASSES, 1);
                 for (uint32_t b0 = 0; b0 < ln && !broken; b0 += 128) {
                     ulonglong2 r[4];
                     bool mine[4];
@@ -1128,6 +1171,7 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
                             }
                             const uint32_t k = (uint32_t)(kd >> 32);
                             const uint64_t d = (uint32_t)kd;
+                            if (lane == 0) stat_add(A, STAT_OUT_RECS, 1);
                             for (uint32_t i = 0; i < k; i++) {
                                 const uint64_t q = p + i * d;
                                 if (q != flo) emit(q - flo);
@@ -1142,6 +1186,7 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
         }
         if ((uint32_t)lane < nb && kb + lane < A.capacity) A.out[kb + lane] = held;
         kb += nb;
+        if (lane == 0) stat_add(A, STAT_CYC_OUTPUT, (unsigned long long)(clock64() - t_seg));
         if (lane == 0) {
             if (kb - excl != cnt || (!first && !(geo & GEO_EMPTY) && st->entry_pos < seg_lo)) {
                 atomicOr(&A.ctrl->err, ERR_INTERNAL);
