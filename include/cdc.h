@@ -157,21 +157,27 @@ typedef enum {
     CDC_OPT_STATS = 6,        /* 1 = the chain stage counts its work (chain
                                  steps, stitch walks, uncovered entries, ...)
                                  for cdc_stats; costs atomics, testing only */
-    CDC_OPT_WARP_CHAINS = 7   /* speculative chains of a segment are stepped one
+    CDC_OPT_WARP_CHAINS = 7,  /* speculative chains of a segment are stepped one
                                  per thread while more than this many are
                                  alive, then one per warp (all 32 lanes share
                                  each step); 1..128, 0 = automatic (96) */
+    CDC_OPT_STARTS = 8        /* distinct speculative starts per segment, spread
+                                 over its first `span` bytes; 1..128, 0 =
+                                 automatic (span / 128, within 16..128) */
 } cdc_option;
 
 CDC_API cdc_status cdc_set_option(cdc_handle h, cdc_option opt, int64_t value);
 CDC_API cdc_status cdc_get_option(cdc_handle h, cdc_option opt, int64_t* value);
 
-/* Autotuner for the segment size and the warp-chain threshold: runs the
- * chunk path on the caller's input for each pair of a small grid (segment
- * bytes: automatic, 128 KiB, 256 KiB, 512 KiB, 1 MiB; warp chains: 32, 64, 96),
- * twice each, timed with CUDA events on `stream`, and keeps the fastest pair on
- * the handle (CDC_OPT_SEGMENT, CDC_OPT_WARP_CHAINS), reported in *seg_out,
- * *warp_chains_out and *best_ms (each may be NULL). Every setting gives the
+/* Autotuner for the segment size, the warp-chain threshold and the number
+ * of speculative starts: runs the chunk path on the caller's input for each
+ * pair of a small grid (segment bytes: automatic, 128 KiB, 256 KiB, 512 KiB,
+ * 1 MiB; warp chains: 32, 64, 96; automatic starts), then for 32, 64 and 128
+ * starts at the best pair, twice each, timed with CUDA events on `stream`, and
+ * keeps the fastest setting on the handle (CDC_OPT_SEGMENT,
+ * CDC_OPT_WARP_CHAINS, CDC_OPT_STARTS, the last readable with
+ * cdc_get_option), reported in *seg_out, *warp_chains_out and *best_ms (each
+ * may be NULL). Every setting gives the
  * same boundaries, so tuning never changes results. d_file_off / n_files /
  * d_bounds_index as for cdc_chunk_batch (d_file_off NULL: one stream of len
  * bytes); d_bounds (capacity entries) is overwritten. Not during stream

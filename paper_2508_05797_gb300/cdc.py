@@ -17,6 +17,7 @@ OPT_SEGMENT, OPT_SPAN, OPT_TIMEOUT_MS, OPT_FORCE_BYTES, OPT_DEBUG_HOLD_ITEM = ra
 OPT_PROFILE = 5
 OPT_STATS = 6
 OPT_WARP_CHAINS = 7
+OPT_STARTS = 8
 STAT_NAMES = ["segments", "thread_steps", "warp_steps", "merges", "stitch_walks", "stitch_steps", "unknown",
               "hash_full", "scan_follows", "out_steps", "empty", "survivors", "cyc_setup", "cyc_threads",
               "cyc_warps", "cyc_stitch", "rounds", "cyc_rounds", "cyc_surv", "stitch_long", "stitch_maxw",

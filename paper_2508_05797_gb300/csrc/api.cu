@@ -45,6 +45,7 @@ struct cdc_handle_s {
     Ctrl* pinned_ctrl = nullptr;  // page-locked copy of the control block
     // options
     int64_t seg = 0, span = 0, timeout_ms = 2000, force_bytes = 0, hold_item = -1, stats = 0, warp_chains = 0;
+    int64_t starts = 0;
     // last-call bookkeeping
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // start, summaries done, end, speculation done
     bool timed = false;
@@ -173,6 +174,10 @@ extern "C" cdc_status cdc_set_option(cdc_handle h, cdc_option opt, int64_t v) {
         if (v < 0 || v > NL) return CDC_ERR_INVALID;
         h->warp_chains = v;
         return CDC_OK;
+    case CDC_OPT_STARTS:
+        if (v < 0 || v > NL) return CDC_ERR_INVALID;
+        h->starts = v;
+        return CDC_OK;
     case CDC_OPT_PROFILE:
         if (v && !h->prof_ev) {
             cudaSetDevice(h->device);
@@ -200,6 +205,7 @@ extern "C" cdc_status cdc_get_option(cdc_handle h, cdc_option opt, int64_t* v) {
     case CDC_OPT_PROFILE: *v = h->profile; return CDC_OK;
     case CDC_OPT_STATS: *v = h->stats; return CDC_OK;
     case CDC_OPT_WARP_CHAINS: *v = h->warp_chains; return CDC_OK;
+    case CDC_OPT_STARTS: *v = h->starts; return CDC_OK;
     default: return CDC_ERR_INVALID;
     }
 }
@@ -255,6 +261,17 @@ static uint64_t pick_seg(cdc_handle h, uint64_t len, uint64_t n_files) {
     uint64_t s = per < (32u << 10) ? (32u << 10) : per;
     if (s > (256u << 10)) s = 256u << 10;
     return (s + 63) & ~63ull;
+}
+
+// distinct speculative starts: about one per 128 bytes of span (measured best
+// on the mixed stream for RAM and AE at 4, 8 and 16 KiB means; MAXP chains
+// join within a chunk and do not care)
+static uint32_t pick_starts(cdc_handle h, uint64_t span) {
+    if (h->starts) return (uint32_t)h->starts;
+    uint64_t n = span / 128;
+    if (n < 16) n = 16;
+    if (n > (uint64_t)NL) n = NL;
+    return (uint32_t)n;
 }
 
 static uint64_t pick_span(cdc_handle h, cdc_params p, uint64_t seg) {
@@ -394,6 +411,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     c.hold_item = h->hold_item;
     c.stats = (int)h->stats;
     c.warp_chains = h->warp_chains ? (uint32_t)h->warp_chains : 96u;
+    c.starts = pick_starts(h, c.span);
     if (h->stats) cudaMemsetAsync(h->ctrl->stats, 0, sizeof(h->ctrl->stats), st);
     if (pl.sum != SUM_NONE) {
         const uint64_t mx4k = ((uint64_t)p.max + 4095) & ~4095ull;
@@ -554,15 +572,28 @@ extern "C" cdc_status cdc_autotune(cdc_handle h, cdc_alg alg, cdc_params p, cons
     cudaSetDevice(h->device);
     static const int64_t kSeg[] = {0, 128 << 10, 256 << 10, 512 << 10, 1 << 20};
     static const int64_t kWarp[] = {32, 64, 96};
-    const int64_t seg0 = h->seg, wc0 = h->warp_chains, prof0 = h->profile;
+    static const int64_t kStarts[] = {32, 64, 128};
+    const int64_t seg0 = h->seg, wc0 = h->warp_chains, ns0 = h->starts, prof0 = h->profile;
     h->profile = 0;
     float best = -1.0f;
-    int64_t best_seg = seg0, best_wc = wc0;
+    int64_t best_seg = seg0, best_wc = wc0, best_ns = 0;
     cdc_status err = CDC_OK;
-    for (int64_t sg : kSeg) {
-        for (int64_t wc : kWarp) {
-            h->seg = sg;
-            h->warp_chains = wc;
+    // segment size x warp threshold with the automatic start count, then the
+    // start count on the best of those
+    const int n_grid = (int)(sizeof(kSeg) / sizeof(kSeg[0]) * sizeof(kWarp) / sizeof(kWarp[0]));
+    const int n_starts = (int)(sizeof(kStarts) / sizeof(kStarts[0]));
+    for (int c = 0; c < n_grid + n_starts; c++) {
+        {
+            if (c < n_grid) {
+                h->seg = kSeg[c / 3];
+                h->warp_chains = kWarp[c % 3];
+                h->starts = 0;
+            } else {
+                h->seg = best_seg;
+                h->warp_chains = best_wc;
+                h->starts = kStarts[c - n_grid];
+            }
+            const int64_t sg = h->seg, wc = h->warp_chains, ns = h->starts;
             float t = -1.0f;
             for (int rep = 0; rep < 2 && err == CDC_OK; rep++) {
                 if (batch && cudaMemsetAsync(d_bounds_index, 0, (n_files + 1) * sizeof(uint64_t), st) != cudaSuccess) {
@@ -588,6 +619,7 @@ extern "C" cdc_status cdc_autotune(cdc_handle h, cdc_alg alg, cdc_params p, cons
                 best = t;
                 best_seg = sg;
                 best_wc = wc;
+                best_ns = ns;
             }
         }
         if (err != CDC_OK) break;
@@ -597,10 +629,12 @@ extern "C" cdc_status cdc_autotune(cdc_handle h, cdc_alg alg, cdc_params p, cons
     if (err != CDC_OK) {
         h->seg = seg0;
         h->warp_chains = wc0;
+        h->starts = ns0;
         return err;
     }
     h->seg = best_seg;
     h->warp_chains = best_wc;
+    h->starts = best_ns;
     if (seg_out) *seg_out = best_seg;
     if (warp_chains_out) *warp_chains_out = best_wc;
     if (best_ms) *best_ms = best;
@@ -826,6 +860,7 @@ extern "C" cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t*
     c.n_items = items;
     c.seg = seg;
     c.span = pick_span(&cfg, p, seg);
+    c.starts = pick_starts(&cfg, c.span);
     c.win = pick_win(p, seg);
     c.out = out_bounds;
     c.capacity = *n;

@@ -70,6 +70,7 @@ struct ChainLaunch {
     int64_t hold_item;
     int stats;               // accumulate Ctrl::stats
     uint32_t warp_chains;    // per-thread speculation rounds run while more chains than this are alive
+    uint32_t starts;         // distinct speculative starts per segment (threads beyond repeat them)
 };
 
 // Memo of per-device launch properties: fn(arg) runs once per (device, key, arg).

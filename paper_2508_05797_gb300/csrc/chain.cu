@@ -374,8 +374,10 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
             if (first) {
                 if (tid == 0) start = flo;
             } else {
-                uint64_t d = umin64(A.span, seg_hi - seg_lo) / NL;
-                start = seg_lo + (uint64_t)tid * (d ? d : 1);
+                // threads beyond `starts` repeat a start: they merge on their first hash insert
+                const uint32_t ns = A.starts;
+                uint64_t d = umin64(A.span, seg_hi - seg_lo) / ns;
+                start = seg_lo + (uint64_t)((uint32_t)tid % ns) * (d ? d : 1);
             }
             // rounds of KS per-thread steps; live chains are compacted into the
             // lowest threads after every round so that idle warps issue nothing

@@ -121,6 +121,24 @@ def test_tiny_segments_stress_lookback(ck, seg):
         ck.set_option(OPT_SPAN, 0)
 
 
+@pytest.mark.parametrize("starts", [1, 3, 16, 128])
+def test_speculative_start_counts(ck, starts):
+    """Any number of distinct speculative starts per segment gives the
+    oracle's boundaries (few starts leave most entries to the stitch and the
+    resolution walks)."""
+    from paper_2508_05797_gb300.cdc import OPT_SEGMENT, OPT_STARTS
+    data = synth.mixed_range(9, 64 * MIB, 5 * MIB, 2 * MIB + 77)
+    try:
+        ck.set_option(OPT_STARTS, starts)
+        for seg in (0, 4096):
+            ck.set_option(OPT_SEGMENT, seg)
+            for alg, w, mn, mx in (("ram", 3000, 1024, 16384), ("ae", 3000, 1024, 16384), ("maxp", 120, 1024, 16384)):
+                expect_equal(ck, data, alg, w, mn, mx, offset=1, tag="starts%d/seg%d" % (starts, seg))
+    finally:
+        ck.set_option(OPT_STARTS, 0)
+        ck.set_option(OPT_SEGMENT, 0)
+
+
 def test_byte_rules_equal_summary_rules(ck):
     from paper_2508_05797_gb300.cdc import OPT_FORCE_BYTES
     data = synth.mixed_range(4, 64 * MIB, 5 * MIB, 1 * MIB + 77)
