@@ -439,6 +439,57 @@ def dedup_workload(dev, base_bytes: int = GIB, n_versions: int = 15, reps: int =
     return res
 
 
+def stream_workload(data, dev, pieces_mib=(64, 256), reps: int = 2):
+    """Resumable chunking (cdc_feed_*): the 4 GiB mixed stream handed over in
+    device pieces of a fixed size, RAM and MAXP at 8 KiB mean; GB/s of stream
+    bytes over the whole feed (piece copies into staging and one
+    synchronisation per push included), against one call on the whole
+    stream; `same` checks that the pushes concatenate to the one-call
+    boundaries."""
+    import torch
+
+    from paper_2508_05797_gb300 import Chunker, Feed
+
+    n = data.numel()
+    t = wtable()["mixed_4g_seed1"]
+    res = {"workload": "the %d MiB mixed stream pushed in fixed-size device pieces" % (n >> 20)}
+    ck = Chunker(dev.index)
+    for alg in ("ram", "maxp"):
+        e = t[alg]["8192"]
+        w, mn, mx = e["w"], e["min"], e["max"]
+        whole = ck.chunk(data, alg, w, mn, mx)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        whole = ck.chunk(data, alg, w, mn, mx)
+        e1.record()
+        torch.cuda.synchronize()
+        r = {"one_call_GBps": round(n / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)}
+        f = Feed(ck, alg, w, mn, mx)
+        for pm in pieces_mib:
+            piece = pm * MIB
+            best, same = None, True
+            for rep in range(reps + 1):  # the first pass sizes the staging buffers
+                f.reset()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                got = []
+                for pos in range(0, n, piece):
+                    got.append(f.push(data[pos:pos + piece], final=pos + piece >= n))
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                if rep:
+                    best = dt if best is None else min(best, dt)
+                same = same and bool(torch.equal(torch.cat(got), whole))
+            r["piece_%dMiB" % pm] = {"GBps": round(n / best / 1e9, 1), "pushes": (n + piece - 1) // piece,
+                                     "same": same}
+        f.close()
+        res[alg] = r
+    ck.close()
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -485,6 +536,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-prims", action="store_true", help="skip the EBS / RS measurement")
     ap.add_argument("--no-dedup", action="store_true", help="skip the dedup-shaped versions measurement")
+    ap.add_argument("--no-stream", action="store_true", help="skip the resumable-feed measurement")
     ap.add_argument("--streams", type=int, default=3, help="streams the nine calls of a step are spread over")
     ap.add_argument("--ref-sample-mib", type=int, default=32, help="reference arm: bytes per (alg, mean) pair")
     ap.add_argument("--serving-requests", type=int, default=20_000)
@@ -630,6 +682,8 @@ def main():
         line["e2e"] = {"value": round(ncfg * n * e2e_steps * world / dt / 1e9, 2), "unit": "GB/s",
                        "h2d_bytes_per_step": ncfg * n, "d2h_bytes_per_step": int(d2h),
                        "steps": e2e_steps}
+    if rank == 0 and not args.no_stream:
+        line["stream"] = stream_workload(data, dev)
     if rank == 0 and not args.no_dedup:
         line["dedup"] = dedup_workload(dev)
     if rank == 0 and not args.no_prims:
