@@ -632,9 +632,17 @@ __device__ __forceinline__ void load_segment(const ChainLaunch& A, uint64_t item
     const int tid = threadIdx.x;
     const uint4* src = reinterpret_cast<const uint4*>(A.hash + item * (uint64_t)HSLOTS);
     uint4* dst = reinterpret_cast<uint4*>(sh.ht);
-    for (int i = tid; i < HSLOTS / 2; i += NL) dst[i] = src[i];
-    sh.X[tid] = A.st[item].X[tid];
-    sh.cnt[tid] = A.st[item].cnt[tid];
+    constexpr int PER = HSLOTS / 2 / NL;  // 16-byte loads per thread, all in flight at once
+    static_assert(HSLOTS / 2 % NL == 0, "hash rows split evenly over the threads");
+    uint4 r[PER];
+#pragma unroll
+    for (int k = 0; k < PER; k++) r[k] = src[tid + k * NL];
+    const unsigned long long x = A.st[item].X[tid];
+    const unsigned int c = A.st[item].cnt[tid];
+#pragma unroll
+    for (int k = 0; k < PER; k++) dst[tid + k * NL] = r[k];
+    sh.X[tid] = x;
+    sh.cnt[tid] = c;
 }
 
 // k_stitch: table "predecessor chain -> (chain, boundaries in this segment)"
@@ -874,19 +882,29 @@ __global__ void __launch_bounds__(32) k_compose(ChainLaunch A) {
         unsigned long long cn[4], ps[4];  // ps: position while sl == NONE (off every chain)
 #pragma unroll
         for (int j = 0; j < 4; j++) { sl[j] = (uint32_t)(lane + 32 * j); cn[j] = 0; ps[j] = 0; }
-        uint32_t nt[4], ngeo;
+        // tables of the next PD segments in flight (slot d holds segment i with (i - i0) % PD == d)
+        constexpr uint64_t PD = 4;
+        uint32_t nt[PD][4], ngeo[PD];
 #pragma unroll
-        for (int j = 0; j < 4; j++) nt[j] = A.st[i0].table[lane + 32 * j];
-        ngeo = A.st[i0].geo;
-        for (uint64_t i = i0; i < i1; i++) {
+        for (uint64_t d = 0; d < PD; d++)
+            if (i0 + d < i1) {
+#pragma unroll
+                for (int j = 0; j < 4; j++) nt[d][j] = A.st[i0 + d].table[lane + 32 * j];
+                ngeo[d] = A.st[i0 + d].geo;
+            }
+        for (uint64_t ib = i0; ib < i1; ib += PD)
+#pragma unroll
+        for (uint64_t d = 0; d < PD; d++) {
+            const uint64_t i = ib + d;
+            if (i >= i1) break;
             uint32_t t[4];
 #pragma unroll
-            for (int j = 0; j < 4; j++) t[j] = nt[j];
-            const uint32_t geo = ngeo;
-            if (i + 1 < i1) {  // prefetch the next table
+            for (int j = 0; j < 4; j++) t[j] = nt[d][j];
+            const uint32_t geo = ngeo[d];
+            if (i + PD < i1) {  // prefetch the table PD segments ahead
 #pragma unroll
-                for (int j = 0; j < 4; j++) nt[j] = A.st[i + 1].table[lane + 32 * j];
-                ngeo = A.st[i + 1].geo;
+                for (int j = 0; j < 4; j++) nt[d][j] = A.st[i + PD].table[lane + 32 * j];
+                ngeo[d] = A.st[i + PD].geo;
             }
             if (geo & GEO_EMPTY) continue;
 #pragma unroll
@@ -1022,23 +1040,35 @@ __global__ void __launch_bounds__(32) k_settle(ChainLaunch A) {
             uint32_t my_slot = NONE, my_cnt = 0;
             uint64_t my_pos = 0, my_excl = 0;
             const uint32_t nb = (uint32_t)umin64(32, i1 - b0);
-            uint32_t nt[4];
+            // tables of the next PD segments in flight (slot d holds segment k with k % PD == d)
+            constexpr uint32_t PD = 4;
+            uint32_t nt[PD][4];
 #pragma unroll
-            for (int j = 0; j < 4; j++) nt[j] = A.st[b0].table[lane + 32 * j];
-            for (uint32_t k = 0; k < nb; k++) {
-                const uint64_t i = b0 + k;
-                uint32_t t[4];
+            for (uint32_t d = 0; d < PD; d++)
+                if (d < nb) {
 #pragma unroll
-                for (int j = 0; j < 4; j++) t[j] = nt[j];
-                if (k + 1 < nb) {
-#pragma unroll
-                    for (int j = 0; j < 4; j++) nt[j] = A.st[i + 1].table[lane + 32 * j];
+                    for (int j = 0; j < 4; j++) nt[d][j] = A.st[b0 + d].table[lane + 32 * j];
                 }
-                if (lane == (int)k) { my_slot = slot; my_pos = pos; my_excl = incl; }
-                const uint32_t e = lookup(t[0], t, slot);
-                const uint32_t n = step_with<RULE>(A, i, e, &slot, &pos);
-                incl += n;
-                if (lane == (int)k) my_cnt = n;
+            for (uint32_t k0 = 0; k0 < nb; k0 += PD) {
+#pragma unroll
+                for (uint32_t d = 0; d < PD; d++) {
+                    const uint32_t k = k0 + d;
+                    if (k < nb) {
+                        const uint64_t i = b0 + k;
+                        uint32_t t[4];
+#pragma unroll
+                        for (int j = 0; j < 4; j++) t[j] = nt[d][j];
+                        if (k + PD < nb) {
+#pragma unroll
+                            for (int j = 0; j < 4; j++) nt[d][j] = A.st[i + PD].table[lane + 32 * j];
+                        }
+                        if (lane == (int)k) { my_slot = slot; my_pos = pos; my_excl = incl; }
+                        const uint32_t e = lookup(t[0], t, slot);
+                        const uint32_t n = step_with<RULE>(A, i, e, &slot, &pos);
+                        incl += n;
+                        if (lane == (int)k) my_cnt = n;
+                    }
+                }
             }
             if ((uint32_t)lane < nb) {
                 const uint64_t i = b0 + lane;
@@ -1095,11 +1125,25 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
                 uint64_t wb0 = (seg_lo >> 6) & ~15ull;
                 uint64_t wn = A.win;
                 if (wb0 + wn > A.nblk_pad) wn = A.nblk_pad > wb0 ? ((A.nblk_pad - wb0) & ~15ull) : 0;
-                for (uint64_t o = (uint64_t)lane * 16; o < wn; o += 512) {
-                    *reinterpret_cast<uint4*>(dsm + o) = *reinterpret_cast<const uint4*>(A.smax + wb0 + o);
-                    if (RULE != RULE_MAXP)
-                        *reinterpret_cast<uint4*>(dsm + A.win + o) =
-                            *reinterpret_cast<const uint4*>(A.sarg + wb0 + o);
+                constexpr int US = 4;  // 16-byte loads in flight per lane and array
+                for (uint64_t o0 = (uint64_t)lane * 16; o0 < wn; o0 += 512 * US) {
+                    uint4 m[US], a[US];
+#pragma unroll
+                    for (int u = 0; u < US; u++) {
+                        const uint64_t o = o0 + 512 * u;
+                        if (o < wn) {
+                            m[u] = *reinterpret_cast<const uint4*>(A.smax + wb0 + o);
+                            if (RULE != RULE_MAXP) a[u] = *reinterpret_cast<const uint4*>(A.sarg + wb0 + o);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < US; u++) {
+                        const uint64_t o = o0 + 512 * u;
+                        if (o < wn) {
+                            *reinterpret_cast<uint4*>(dsm + o) = m[u];
+                            if (RULE != RULE_MAXP) *reinterpret_cast<uint4*>(dsm + A.win + o) = a[u];
+                        }
+                    }
                 }
                 S.wb0 = wb0;
                 S.wn = wn;
