@@ -388,6 +388,22 @@ def prims_workload(data, dev, n_q: int = 1 << 20, span: int = 8192, reps: int = 
     out["rs_geq"] = {"ms": round(t_rs, 3), "GBps_of_ranges": round(n_q * span / (t_rs / 1e3) / 1e9, 1),
                      "GBps_scanned": round(scanned / (t_rs / 1e3) / 1e9, 1),
                      "same_position": bool(torch.equal(q, p))}
+    # byte shares of the two patterns in RAM and AE at 8 KiB mean (cdc_byte_shares
+    # over the chunk boundaries of the whole stream)
+    from paper_2508_05797_gb300 import byte_shares, chunk
+    shares = {}
+    for alg in ("ram", "ae"):
+        e = wtable()["mixed_4g_seed1"][alg]["8192"]
+        b = chunk(data, alg, e["w"], e["min"], e["max"])
+        byte_shares(data, b, alg, e["w"], e["min"], e["max"])
+        torch.cuda.synchronize()
+        e0.record()
+        es, rb = byte_shares(data, b, alg, e["w"], e["min"], e["max"])
+        e1.record()
+        torch.cuda.synchronize()
+        shares[alg] = {"ebs_pct": round(100.0 * es / max(1, es + rb), 2), "rs_pct": round(100.0 * rb / max(1, es + rb), 2),
+                       "ebs_bytes": es, "rs_bytes": rb, "ms": round(e0.elapsed_time(e1), 3)}
+    out["byte_shares_8k"] = shares
     return out
 
 

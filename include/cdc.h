@@ -277,6 +277,22 @@ CDC_API cdc_status cdc_ebs(cdc_ebs_op op, const uint8_t* data, size_t len, const
 CDC_API cdc_status cdc_rs(cdc_rs_cmp cmp, const uint8_t* data, size_t len, const uint64_t* d_ranges,
                           const uint8_t* d_thresholds, size_t n, uint64_t* d_pos, cdc_stream stream);
 
+/* Bytes read by each of the two processing patterns while the chunks of a
+ * buffer are found, as Section 3.3 composes the algorithms (the paper plots
+ * these shares per algorithm and dataset). d_bounds: the n boundaries
+ * cdc_chunk wrote for `data` with the same alg and p. d_out (device, 2
+ * uint64) receives the bytes read by Extreme Byte Searches, then by Range
+ * Scans. RAM: per chunk one search over its w-byte window (the rest, for a
+ * tail of at most w bytes) and one GEQ scan from max(s + w, s + min - 1) to
+ * the cut. AE-Max / AE-Min: per target (a byte beyond every earlier byte of
+ * the chunk) one search over the w bytes after it, clipped at the chunk's
+ * last byte, and GT / LT scans from target to target. MAXP (the paper does
+ * not say where its scans stop) and AE with min > w + 1 (where the window end
+ * is not always a permitted cut) give CDC_ERR_INVALID. Asynchronous on
+ * `stream`; no handle needed. */
+CDC_API cdc_status cdc_byte_shares(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
+                                   const uint64_t* d_bounds, size_t n, uint64_t* d_out, cdc_stream stream);
+
 /* 128-bit fingerprints of the chunks of a buffer, for deduplication
  * reports: chunk i is [d_bounds[i-1], d_bounds[i]) (d_bounds[-1] = 0; the
  * boundary list cdc_chunk writes, each <= len), its fingerprint d_fp[2i],

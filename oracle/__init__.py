@@ -57,6 +57,8 @@ class Oracle:
         lib.oracle_maxp_targets.restype = u64
         lib.oracle_ebs.argtypes = [i32, vp, u64, u64, u64, ctypes.POINTER(u64)]
         lib.oracle_ebs.restype = u32
+        lib.oracle_byte_shares.argtypes = [i32, vp, u64, u32, u32, u32, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        lib.oracle_byte_shares.restype = i32
         lib.oracle_rs.argtypes = [i32, vp, u64, u64, u64, u32]
         lib.oracle_rs.restype = u64
         self.lib = lib
@@ -115,6 +117,16 @@ class Oracle:
         """First offset in [a, b) whose byte compares true against t, else b."""
         arr = self._buf(data)
         return int(self.lib.oracle_rs(RS_CMPS[cmp], arr.ctypes.data if arr.size else None, arr.size, a, b, t))
+
+    def byte_shares(self, alg, data, w: int, mn: int, mx: int):
+        """(bytes read by Extreme Byte Searches, bytes read by Range Scans)
+        while the whole buffer is chunked, as Section 3.3 composes RAM and AE;
+        None for MAXP or AE with min > w + 1 (undefined there)."""
+        a = self._buf(data)
+        e, r = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        st = self.lib.oracle_byte_shares(alg_id(alg), a.ctypes.data if a.size else None, a.size, w, mn, mx,
+                                         ctypes.byref(e), ctypes.byref(r))
+        return None if st else (int(e.value), int(r.value))
 
     def horizon(self, alg, w: int, mx: int) -> int:
         """Bytes after a chunk start s that decide the chunk from s: RAM and AE
@@ -179,3 +191,7 @@ def maxp_targets(data, w: int) -> np.ndarray:
 
 def chunk_pieces(alg, pieces, w: int, mn: int, mx: int, horizon: int | None = None) -> list:
     return get().chunk_pieces(alg, pieces, w, mn, mx, horizon)
+
+
+def byte_shares(alg, data, w: int, mn: int, mx: int):
+    return get().byte_shares(alg, data, w, mn, mx)

@@ -174,3 +174,67 @@ uint64_t oracle_rs(int cmp, const uint8_t* B, uint64_t len, uint64_t a, uint64_t
     }
     return b;
 }
+
+/* Bytes each processing pattern reads while the chunks of B are found, as
+ * Section 3.3 composes the algorithms (the paper reports these shares in its
+ * byte-share figure). Chunk by chunk from s (e = its end, L = min(len, s + max)):
+ *   RAM: one Extreme Byte Search over the w-byte window at s, then one GEQ
+ *        Range Scan from max(s + w, s + min - 1) up to and including the byte
+ *        it stops at (or up to L when it finds none); a tail of at most w
+ *        bytes is one search over the rest.
+ *   AE:  from the first target s: an Extreme Byte Search over the w bytes
+ *        after the target (clipped at L - 1); if that window holds a byte
+ *        beyond the target, a GT (LT for AE-Min) Range Scan from the target
+ *        finds the next target (the bytes after the target up to it) and the
+ *        search repeats; otherwise the chunk ends after the window. Defined
+ *        for min <= w + 1, where the window end is always a permitted cut.
+ * Adds to *ebs and *rs; returns 0, or -1 for MAXP or AE with min > w + 1. */
+int oracle_byte_shares(int alg, const uint8_t* B, uint64_t len, uint32_t w, uint32_t mn, uint32_t mx,
+                       uint64_t* ebs, uint64_t* rs) {
+    if (alg == OR_MAXP) return -1;
+    if ((alg == OR_AE_MAX || alg == OR_AE_MIN) && mn > w + 1) return -1;
+    uint64_t s = 0;
+    while (s < len) {
+        const uint64_t L = umin(len, s + mx);
+        uint64_t e;
+        if (alg == OR_RAM) {
+            if (len - s <= w) {
+                *ebs += len - s;
+                e = len;
+            } else {
+                uint64_t at;
+                const uint32_t M = oracle_ebs(0, B, len, s, s + w, &at);
+                *ebs += w;
+                const uint64_t from = mn - 1 > w ? s + mn - 1 : s + w;  /* the scan's first byte */
+                if (from >= L) {
+                    e = L;
+                } else {
+                    const uint64_t j = oracle_rs(2, B, len, from, L, M);
+                    e = j < L ? j + 1 : L;
+                    *rs += e - from;
+                }
+            }
+        } else {
+            const int op = alg == OR_AE_MIN ? 1 : 0;     /* window search for max or min */
+            const int cmp = alg == OR_AE_MIN ? 1 : 0;    /* GT or LT */
+            uint64_t p = s;
+            for (;;) {
+                const uint64_t wend = umin(p + w, L - 1);  /* window (p, wend] */
+                uint64_t at;
+                const uint32_t x = oracle_ebs(op, B, len, p + 1, wend + 1, &at);
+                *ebs += wend - p;
+                const int beyond = wend > p && (op ? x < B[p] : x > B[p]);
+                if (!beyond) {
+                    e = p + w < L ? p + w + 1 : L;
+                    break;
+                }
+                const uint64_t r = oracle_rs(cmp, B, len, p + 1, wend + 1, B[p]);
+                *rs += r - p;
+                p = r;
+            }
+        }
+        s = e;
+    }
+    return 0;
+}
+

@@ -89,6 +89,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "cdc_ebs": ([i32, vp, sz, vp, sz, vp, vp, vp], i32),
             "cdc_rs": ([i32, vp, sz, vp, vp, sz, vp, vp], i32),
             "cdc_fingerprint": ([vp, sz, vp, sz, vp, vp], i32),
+            "cdc_byte_shares": ([i32, P, vp, sz, vp, sz, vp, vp], i32),
             "cdc_feed_create": ([ctypes.POINTER(vp), vp, i32, P], i32),
             "cdc_feed_push": ([vp, vp, sz, i32, vp, ctypes.POINTER(sz), vp], i32),
             "cdc_feed_position": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64)], i32),
@@ -112,7 +113,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return ["cdc_create", "cdc_destroy", "cdc_chunk", "cdc_chunk_async", "cdc_chunk_batch", "cdc_chunk_host",
             "cdc_reserve", "cdc_sync_status", "cdc_set_option", "cdc_get_option", "cdc_last_timing",
-            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_ebs", "cdc_rs", "cdc_fingerprint", "cdc_feed_create", "cdc_feed_push",
+            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_ebs", "cdc_rs", "cdc_fingerprint", "cdc_byte_shares", "cdc_feed_create", "cdc_feed_push",
             "cdc_feed_position", "cdc_feed_reset", "cdc_feed_destroy", "cdc_server_create", "cdc_server_submit",
             "cdc_server_poll", "cdc_server_clock", "cdc_server_destroy", "cdc_status_string"]
 
@@ -443,6 +444,21 @@ def fingerprint(data, bounds, stream=None):
                                           b.data_ptr() if n else None, n, fp.data_ptr() if n else None,
                                           _stream_handle(stream)), "cdc_fingerprint")
     return fp
+
+
+def byte_shares(data, bounds, alg, w: int, mn: int, mx: int, stream=None):
+    """(bytes read by Extreme Byte Searches, bytes read by Range Scans) while
+    the chunks `bounds` of `data` were found (cdc_byte_shares)."""
+    import torch
+    lib = load_library()
+    assert data.dtype == torch.uint8 and data.is_cuda
+    out = torch.empty(2, dtype=torch.int64, device=data.device)
+    n = bounds.numel()
+    _check(lib.cdc_byte_shares(alg_id(alg), Params(w, mn, mx), data.data_ptr() if data.numel() else None,
+                               data.numel(), bounds.data_ptr() if n else None, n, out.data_ptr(),
+                               _stream_handle(stream)), "cdc_byte_shares")
+    v = out.cpu().tolist()
+    return v[0], v[1]
 
 
 def dedup_report(pieces):

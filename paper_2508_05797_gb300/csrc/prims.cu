@@ -248,8 +248,93 @@ __global__ void k_fingerprint(const uint8_t* base, uint64_t lo, const uint64_t* 
     }
 }
 
+// Byte shares of the two processing patterns (Section 3.3's composition),
+// from the boundaries: one warp per chunk [s, e).
+//   RAM: search w bytes (the rest for a tail of at most w), scan
+//        e - max(s + w, s + min - 1).
+//   AE:  the targets are the bytes beyond every earlier byte of the chunk
+//        (positions p in [s, e) with B[p] beyond max B[s, p)); each target's
+//        window search reads min(w, e - 1 - p) bytes, the scans from target to
+//        target read (last target) - s.
+// Targets come 32 bytes at a time: a warp max-scan of (byte + 1) gives the
+// maximum before each lane, carried across rounds. Totals go to out[0..1]
+// with one atomic per warp.
+__global__ void k_byte_shares(int alg, const uint8_t* data, uint64_t len, const uint64_t* bounds, uint64_t n,
+                              uint32_t w, uint32_t mn, unsigned long long* out) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t inv = alg == CDC_AE_MIN ? 0xFFu : 0u;
+    unsigned long long ebs = 0, rs = 0;
+    for (uint64_t c = warp; c < n; c += nwarps) {
+        const uint64_t s = c ? bounds[c - 1] : 0, e = bounds[c];
+        if (e <= s || e > len) continue;
+        if (alg == CDC_RAM) {
+            if (lane == 0) {
+                if (len - s <= w) {
+                    ebs += len - s;
+                } else {
+                    ebs += w;
+                    const uint64_t from = s + w > s + mn - 1 ? s + w : s + mn - 1;
+                    if (e > from) rs += e - from;
+                }
+            }
+            continue;
+        }
+        uint32_t carry = 0;   // (max byte so far) + 1; 0 before the first byte
+        uint64_t last = s;    // last target seen by this lane
+        for (uint64_t b0 = s; b0 < e; b0 += 32) {
+            const uint64_t p = b0 + (uint64_t)lane;
+            const uint32_t v = p < e ? ((uint32_t)(data[p] ^ inv) + 1u) : 0u;
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULLMASK, incl, o);
+                if (lane >= o) incl = max(incl, t);
+            }
+            uint32_t before = __shfl_up_sync(FULLMASK, incl, 1);
+            if (lane == 0) before = 0;
+            before = max(before, carry);
+            if (v > before) {  // a target
+                const uint64_t room = e - 1 - p;
+                ebs += room < w ? room : w;
+                last = p;
+            }
+            carry = max(carry, __shfl_sync(FULLMASK, incl, 31));
+        }
+        // the chunk's last target: the largest position any lane saw
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t t = __shfl_xor_sync(FULLMASK, last, o);
+            last = t > last ? t : last;
+        }
+        if (lane == 0) rs += last - s;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ebs += __shfl_xor_sync(FULLMASK, ebs, o);
+        rs += __shfl_xor_sync(FULLMASK, rs, o);
+    }
+    if (lane == 0 && (ebs || rs)) {
+        atomicAdd(&out[0], ebs);
+        atomicAdd(&out[1], rs);
+    }
+}
+
 }  // namespace
 }  // namespace cdc
+
+extern "C" cdc_status cdc_byte_shares(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
+                                      const uint64_t* d_bounds, size_t n, uint64_t* d_out, cdc_stream stream) {
+    if ((int)alg < 0 || (int)alg > 3 || !d_out || (n && !d_bounds) || (len && !data)) return CDC_ERR_INVALID;
+    if (alg == CDC_MAXP || ((alg == CDC_AE || alg == CDC_AE_MIN) && p.min > p.w + 1)) return CDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(d_out, 0, 2 * sizeof(uint64_t), st) != cudaSuccess) return CDC_ERR_CUDA;
+    if (n == 0) return CDC_OK;
+    cdc::k_byte_shares<<<cdc::grid_for(n), 256, 0, st>>>((int)alg, data, len, d_bounds, n, p.w, p.min,
+                                                          reinterpret_cast<unsigned long long*>(d_out));
+    return cudaGetLastError() == cudaSuccess ? CDC_OK : CDC_ERR_CUDA;
+}
 
 extern "C" cdc_status cdc_fingerprint(const uint8_t* data, size_t len, const uint64_t* d_bounds, size_t n,
                                       uint64_t* d_fp, cdc_stream stream) {

@@ -61,3 +61,20 @@ def test_empty_inputs():
     assert v.cpu().tolist() == [255, 255] and p.cpu().tolist() == [0, 3]
     q = pkg.rs(d, r, torch.tensor([0, 0], dtype=torch.uint8, device="cuda"), "geq")
     assert q.cpu().tolist() == [10, 3]
+
+
+@pytest.mark.parametrize("offset", [0, 3])
+def test_byte_shares_match_oracle(offset):
+    """cdc_byte_shares over the GPU's boundaries equals the oracle's search /
+    scan loop exactly (RAM, AE-Max, AE-Min; several windows)."""
+    import paper_2508_05797_gb300 as pkg
+    from paper_2508_05797_gb300.cdc import CdcError, ERR_INVALID
+    data = synth.mixed_range(12, 64 << 20, 7 << 20, 6 << 20)
+    d = to_device(data, offset)
+    for alg, w, mn, mx in (("ram", 7936, 2048, 65536), ("ram", 100, 500, 3000), ("ae", 7000, 2048, 65536),
+                           ("ae", 64, 32, 700), ("ae_min", 3000, 1024, 20000)):
+        b = pkg.chunk(d, alg, w, mn, mx)
+        assert pkg.byte_shares(d, b, alg, w, mn, mx) == oracle.byte_shares(alg, data, w, mn, mx), (alg, w)
+    with pytest.raises(CdcError) as ei:
+        pkg.byte_shares(d, pkg.chunk(d, "maxp", 300, 2048, 65536), "maxp", 300, 2048, 65536)
+    assert ei.value.status == ERR_INVALID
