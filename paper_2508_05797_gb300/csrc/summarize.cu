@@ -161,7 +161,7 @@ constexpr int MP_THREADS = 256;
 constexpr int MP_TILE_BLOCKS = 256;  // 16 KiB of targets per tile
 
 // Dynamic shared memory: 2 stages of (MP_TILE_BLOCKS + 2*hb) * 64 bytes, then
-// per-stage-block max / first / last arrays, then 2 mbarriers.
+// per-stage-block max / first-position arrays (and one spare), then 2 mbarriers.
 __global__ void __launch_bounds__(MP_THREADS, 4) k_summary_maxp(SumLaunch a) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
@@ -171,12 +171,14 @@ __global__ void __launch_bounds__(MP_THREADS, 4) k_summary_maxp(SumLaunch a) {
     uint8_t* buf = smem;
     uint8_t* bm = smem + 2 * sbytes;
     uint8_t* bf = bm + nb;
-    uint8_t* bl = bf + nb;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + ((2 * sbytes + 3 * nb + 15) & ~15u));
     __shared__ unsigned int supcnt[MP_TILE_BLOCKS / 64];
     __shared__ uint16_t qlist[MP_TILE_BLOCKS];  // candidates waiting for a byte test of their end blocks
     __shared__ uint8_t qres[MP_TILE_BLOCKS];
     __shared__ unsigned int qn;
+    __shared__ uint16_t slist[MP_TILE_BLOCKS];  // blocks that passed the prefilter
+    __shared__ uint8_t tstate[MP_TILE_BLOCKS];  // 0: no target, 1: target, 2: queued for byte tests
+    __shared__ unsigned int sn;
     if (blockIdx.x == 0 && tid == 0) reset_ctrl(a.ctrl);
     const uint64_t ntiles = (a.nblk + MP_TILE_BLOCKS - 1) / MP_TILE_BLOCKS;
     if (tid == 0) {
@@ -210,6 +212,8 @@ __global__ void __launch_bounds__(MP_THREADS, 4) k_summary_maxp(SumLaunch a) {
         }
     }
     const uint32_t w = a.w;
+    // blocks this close to a block lie inside the window of any byte of it
+    const uint32_t K = w >= 63 ? (w - 63) / 64 : 0;
     uint32_t i = 0;
     for (uint64_t t = blockIdx.x; t < ntiles; t += g, i++) {
         const int s = i & 1;
@@ -222,41 +226,59 @@ __global__ void __launch_bounds__(MP_THREADS, 4) k_summary_maxp(SumLaunch a) {
         }
         const uint8_t* tb = buf + s * sbytes;
         const int64_t sb0 = (int64_t)(t * MP_TILE_BLOCKS) - (int64_t)hb;  // global block of stage block 0
-        // 1) block max, first and last position of the max, for every stage block
+        // 1) block max and first position of the max, for every stage block
         for (uint32_t sb = tid; sb < nb; sb += MP_THREADS) {
             const int64_t gblk = sb0 + (int64_t)sb;
-            uint32_t kf = 0, kl = 0;
-            if (gblk >= 0) {  // blocks before position 0 stay all-zero
+            uint32_t kf = 255u;  // blocks before position 0: max 0, first position 0
+            if (gblk >= 0) {
                 const uint64_t P0 = (uint64_t)gblk * 64;
                 const bool edge = P0 < a.lo || P0 + 64 > a.hi;
                 kf = block_key<false>(tb + 64 * sb, (sb >> 1) & 3u, 0u, edge, P0, a.lo, a.hi);
-                kl = block_key<true>(tb + 64 * sb, (sb >> 1) & 3u, 0u, edge, P0, a.lo, a.hi);
-            } else {
-                kf = 255u;  // max 0, first position 0
             }
             bm[sb] = (uint8_t)(kf >> 8);
             bf[sb] = (uint8_t)(255u - (kf & 0xFFu));
-            bl[sb] = (uint8_t)(kl & 0xFFu);
         }
+        if (tid == 0) sn = 0;
         __syncthreads();
-        // 2) target test, one thread per tile block. Interior blocks of the
-        // window are judged by their maxima; a candidate whose partial end
-        // blocks may hold a byte >= its value is queued, and whole warps test
-        // those bytes (16 lanes per end block).
+        // 2) prefilter, one thread per tile block: the blocks within K of it lie
+        // inside the window wherever the maximum sits in its block, so none of
+        // them may reach its maximum. Survivors (a small share) are listed.
         static_assert(MP_TILE_BLOCKS == MP_THREADS, "one tile block per thread");
-        uint32_t state = 0;  // 0: no target, 1: target, 2: queued
         {
             const uint32_t lb = (uint32_t)tid;
             const uint64_t gb = t * MP_TILE_BLOCKS + lb;
-            const uint32_t sbi = hb + lb;  // stage index of this block
+            const uint32_t sbi = hb + lb;
             const uint32_t v = bm[sbi];
-            const uint64_t p = gb * 64 + bf[sbi];
-            if (gb < a.nblk && v != 0 && bf[sbi] == bl[sbi] && p >= a.lo + w && p + w < a.hi) {
+            bool pass = gb < a.nblk && v != 0;
+            for (uint32_t k = 1; k <= K && pass; k++)
+                if (bm[sbi - k] >= v || bm[sbi + k] >= v) pass = false;
+            tstate[lb] = 0;
+            if (pass) slist[atomicAdd(&sn, 1u)] = (uint16_t)lb;
+        }
+        __syncthreads();
+        // 3) survivors: a unique maximum (its last position equals its first),
+        // both windows inside the data, the remaining interior blocks of the
+        // window below it; a survivor whose partial end blocks may hold a byte
+        // >= its value is queued, and whole warps test those bytes (16 lanes
+        // per end block).
+        for (uint32_t k = tid; k < sn; k += MP_THREADS) {
+            const uint32_t lb = slist[k];
+            const uint64_t gb = t * MP_TILE_BLOCKS + lb;
+            const uint32_t sbi = hb + lb;
+            const uint64_t P0 = gb * 64;
+            const bool edge = P0 < a.lo || P0 + 64 > a.hi;
+            const uint32_t kl = block_key<true>(tb + 64 * sbi, (sbi >> 1) & 3u, 0u, edge, P0, a.lo, a.hi);
+            const uint32_t v = bm[sbi];
+            const uint64_t p = P0 + bf[sbi];
+            uint32_t state = 0;  // 0: no target, 1: target, 2: queued
+            if (bf[sbi] == (kl & 0xFFu) && p >= a.lo + w && p + w < a.hi) {
                 const uint64_t wl = p - w, wr = p + w;  // window [wl, wr]
                 const uint32_t s0 = (uint32_t)((int64_t)(wl >> 6) - sb0), s1 = (uint32_t)((int64_t)(wr >> 6) - sb0);
                 bool ok = true;
-                for (uint32_t si = s0 + 1; si < s1 && ok; si++)
-                    if (si != sbi && bm[si] >= v) ok = false;
+                for (uint32_t si = s0 + 1; si < sbi - K && ok; si++)
+                    if (bm[si] >= v) ok = false;
+                for (uint32_t si = sbi + K + 1; si < s1 && ok; si++)
+                    if (bm[si] >= v) ok = false;
                 bool queue = false;
                 if (ok && s0 != sbi && bm[s0] >= v) {
                     if ((wl & 63) == 0) ok = false;  // the whole block lies in the window
@@ -268,6 +290,7 @@ __global__ void __launch_bounds__(MP_THREADS, 4) k_summary_maxp(SumLaunch a) {
                 }
                 state = ok ? (queue ? 2u : 1u) : 0u;
             }
+            tstate[lb] = (uint8_t)state;
             if (state == 2) qlist[atomicAdd(&qn, 1u)] = (uint16_t)lb;
         }
         __syncthreads();
@@ -291,9 +314,9 @@ __global__ void __launch_bounds__(MP_THREADS, 4) k_summary_maxp(SumLaunch a) {
                 if (4 * j + 3 < o0 || 4 * j > o1) x = 0;
                 if (4 * j < o0 && 4 * j + 3 >= o0) x &= 0xFFFFFFFFu << (8 * (o0 - 4 * j));
                 if (4 * j <= o1 && 4 * j + 3 > o1) x &= 0xFFFFFFFFu >> (8 * (4 * j + 3 - o1));
-                const uint32_t K = (0x8000u - v) * 0x00010001u;
+                const uint32_t Kv = (0x8000u - v) * 0x00010001u;
                 const uint32_t e = __byte_perm(x, 0, 0x4240), o = __byte_perm(x, 0, 0x4341);
-                f = ((e + K) | (o + K)) & 0x80008000u;
+                f = ((e + Kv) | (o + Kv)) & 0x80008000u;
             }
             const uint32_t bal = __ballot_sync(FULL, f != 0);
             if (lane == 0) qres[lb] = bal == 0 ? 1 : 0;
@@ -302,6 +325,7 @@ __global__ void __launch_bounds__(MP_THREADS, 4) k_summary_maxp(SumLaunch a) {
         {
             const uint32_t lb = (uint32_t)tid;
             const uint64_t gb = t * MP_TILE_BLOCKS + lb;
+            const uint32_t state = tstate[lb];
             const bool ok = state == 1 || (state == 2 && qres[lb]);
             if (gb < a.nblk) a.smax[gb] = ok ? bf[hb + lb] : (uint8_t)0xFFu;
             // targets per 4 KiB superblock (64 blocks = 2 warps)
