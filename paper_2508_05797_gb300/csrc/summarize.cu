@@ -162,7 +162,7 @@ constexpr int MP_TILE_BLOCKS = 256;  // 16 KiB of targets per tile
 
 // Dynamic shared memory: 2 stages of (MP_TILE_BLOCKS + 2*hb) * 64 bytes, then
 // per-stage-block max / first-position arrays (and one spare), then 2 mbarriers.
-__global__ void __launch_bounds__(MP_THREADS, 4) k_summary_maxp(SumLaunch a) {
+__global__ void __launch_bounds__(MP_THREADS, 6) k_summary_maxp(SumLaunch a) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
     const uint32_t hb = a.halo_blocks;
