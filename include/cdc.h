@@ -171,8 +171,8 @@ CDC_API cdc_status cdc_get_option(cdc_handle h, cdc_option opt, int64_t* value);
 
 /* Autotuner for the segment size, the warp-chain threshold and the number
  * of speculative starts: runs the chunk path on the caller's input for each
- * pair of a small grid (segment bytes: automatic, 128 KiB, 256 KiB, 512 KiB,
- * 1 MiB; warp chains: 32, 64, 96; automatic starts), then for 32, 64 and 128
+ * pair of a small grid (segment bytes: automatic, 128 KiB, 256 KiB, 384 KiB,
+ * 512 KiB, 1 MiB; warp chains: 32, 64, 96; automatic starts), then for 32, 64 and 128
  * starts at the best pair, twice each, timed with CUDA events on `stream`, and
  * keeps the fastest setting on the handle (CDC_OPT_SEGMENT,
  * CDC_OPT_WARP_CHAINS, CDC_OPT_STARTS, the last readable with

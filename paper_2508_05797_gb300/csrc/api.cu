@@ -254,12 +254,18 @@ static Plan make_plan(cdc_handle h, cdc_alg alg, cdc_params p) {
     return pl;
 }
 
-// segment size: a few segments per resident warp, 64-byte multiple
-static uint64_t pick_seg(cdc_handle h, uint64_t len, uint64_t n_files) {
+// segment size: a few segments per resident warp, 64-byte multiple. Longer
+// segments let more speculative chains join inside them; the cap keeps the
+// staged summary window (segment + bound room + max, two bytes per block for
+// RAM / AE, one for MAXP) small enough for five or six resident speculation
+// blocks per SM. Caps measured on the 4 GiB mixed stream: 384 KiB for RAM / AE
+// up to max = 64 KiB, 256 KiB above, 512 KiB for MAXP.
+static uint64_t pick_seg(cdc_handle h, cdc_alg alg, cdc_params p, uint64_t len, uint64_t n_files) {
     if (h->seg) return (uint64_t)h->seg;
+    const uint64_t cap = alg == CDC_MAXP ? (512u << 10) : p.max >= (128u << 10) ? (256u << 10) : (384u << 10);
     uint64_t per = len / ((uint64_t)(h->sm_count > 0 ? h->sm_count : 148) * 16 + n_files);
     uint64_t s = per < (32u << 10) ? (32u << 10) : per;
-    if (s > (256u << 10)) s = 256u << 10;
+    if (s > cap) s = cap;
     return (s + 63) & ~63ull;
 }
 
@@ -321,7 +327,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     // summaries cover the context bytes before data too (ctx > 0: one stream only)
     const Geo g = geometry(data - ctx, len + ctx);
     const bool batch = d_file_off != nullptr;
-    const uint64_t seg = pick_seg(h, len, batch ? n_files : 1);
+    const uint64_t seg = pick_seg(h, alg, p, len, batch ? n_files : 1);
     const uint64_t items = batch ? len / seg + n_files + 1 : (len + seg - 1) / seg;
     cdc_status s;
     if (pl.sum != SUM_NONE) {
@@ -570,7 +576,7 @@ extern "C" cdc_status cdc_autotune(cdc_handle h, cdc_alg alg, cdc_params p, cons
     cudaStream_t st = (cudaStream_t)stream;
     if (capturing(st)) return CDC_ERR_INVALID;
     cudaSetDevice(h->device);
-    static const int64_t kSeg[] = {0, 128 << 10, 256 << 10, 512 << 10, 1 << 20};
+    static const int64_t kSeg[] = {0, 128 << 10, 256 << 10, 384 << 10, 512 << 10, 1 << 20};
     static const int64_t kWarp[] = {32, 64, 96};
     static const int64_t kStarts[] = {32, 64, 128};
     const int64_t seg0 = h->seg, wc0 = h->warp_chains, ns0 = h->starts, prof0 = h->profile;
@@ -646,7 +652,7 @@ extern "C" cdc_status cdc_reserve(cdc_handle h, cdc_alg alg, cdc_params p, size_
     cudaSetDevice(h->device);
     const Plan pl = make_plan(h, alg, p);
     const uint64_t nblk_pad = ((len + 64 + 63) / 64 + 15) & ~15ull;
-    const uint64_t seg = pick_seg(h, len, n_files ? n_files : 1);
+    const uint64_t seg = pick_seg(h, alg, p, len, n_files ? n_files : 1);
     const uint64_t items = len / seg + n_files + 2;
     cdc_status s;
     if (pl.sum != SUM_NONE) {
@@ -815,7 +821,7 @@ extern "C" cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t*
     cudaDeviceGetAttribute(&cfg.sm_count, cudaDevAttrMultiProcessorCount, dev);
     const Plan pl = make_plan(&cfg, alg, p);
     const Geo g = geometry(data, len);
-    const uint64_t seg = pick_seg(&cfg, len, 1);
+    const uint64_t seg = pick_seg(&cfg, alg, p, len, 1);
     const uint64_t items = (len + seg - 1) / seg;
     if (items > kFixItems || g.nblk_pad + 64 > kFixSumBytes || g.nsup + 64 > kFixSupBytes) return CDC_ERR_INTERNAL;
     const uint64_t timeout_ns = (uint64_t)cfg.timeout_ms * 1000000ull;
