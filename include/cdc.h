@@ -210,7 +210,8 @@ CDC_API cdc_status cdc_profile_collect(cdc_handle h, int* calls, double* summary
  * resolution, stitching), per-thread rounds, the cycles of the rounds and of
  * the one-warp-per-chain phase, stitch walks of more than 64 steps,
  * (steps << 32 | segment) of the longest one, the output kernel's passes over
- * step logs, records it replayed and its cycles (24 counters).
+ * step logs, records it replayed, its cycles and the part of them spent in
+ * its own chain steps (25 counters).
  * Synchronises `stream`. */
 CDC_API cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream stream);
 
@@ -251,7 +252,7 @@ CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
  *     wrong results. Serialise them.
  */
 #define CDC_STATIC_MAX_LEN ((size_t)16 << 20)
-#define CDC_STATIC_SCRATCH_BYTES ((size_t)19190528)
+#define CDC_STATIC_SCRATCH_BYTES ((size_t)21554432)
 
 CDC_API cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
                                     uint64_t* out_bounds, size_t* n, cdc_stream stream);

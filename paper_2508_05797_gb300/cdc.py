@@ -21,7 +21,7 @@ OPT_STARTS = 8
 STAT_NAMES = ["segments", "thread_steps", "warp_steps", "merges", "stitch_walks", "stitch_steps", "unknown",
               "hash_full", "scan_follows", "out_steps", "empty", "survivors", "cyc_setup", "cyc_threads",
               "cyc_warps", "cyc_stitch", "rounds", "cyc_rounds", "cyc_surv", "stitch_long", "stitch_maxw",
-              "out_passes", "out_recs", "cyc_output"]
+              "out_passes", "out_recs", "cyc_output", "cyc_out_steps"]
 STATUS = ["CDC_OK", "CDC_ERR_INVALID", "CDC_ERR_CAPACITY", "CDC_ERR_CUDA", "CDC_ERR_TIMEOUT",
           "CDC_ERR_NOMEM", "CDC_ERR_INTERNAL"]
 OK, ERR_INVALID, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_INTERNAL = range(7)

@@ -226,6 +226,7 @@ struct Plan {
 };
 
 static constexpr uint32_t MAXP_SUMMARY_MAX_W = 16384;
+static constexpr uint32_t kLogCap = HANDLE_LOG_CAP;
 
 static Plan make_plan(cdc_handle h, cdc_alg alg, cdc_params p) {
     Plan pl{SUM_NONE, RULE_RAM_BYTES, 0u, 0u};
@@ -338,7 +339,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     }
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, st)) != CDC_OK) return s;
     if ((s = grow(&h->hash, &h->hash_cap, items * seg_hash_bytes(), false, st)) != CDC_OK) return s;
-    if ((s = grow(&h->plog, &h->plog_cap, items * seg_log_bytes(), false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->plog, &h->plog_cap, items * seg_log_bytes(kLogCap), false, st)) != CDC_OK) return s;
     if ((s = grow(&h->groups, &h->groups_cap, ((items + GS - 1) / GS + 1) * group_state_bytes(), false, st)) !=
         CDC_OK)
         return s;
@@ -411,6 +412,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     c.st = reinterpret_cast<SegState*>(h->st);
     c.hash = reinterpret_cast<unsigned long long*>(h->hash);
     c.plog = reinterpret_cast<unsigned long long*>(h->plog);
+    c.logcap = kLogCap;
     c.groups = h->groups;
     c.ctrl = h->ctrl;
     c.timeout_ns = timeout_ns;
@@ -662,7 +664,7 @@ extern "C" cdc_status cdc_reserve(cdc_handle h, cdc_alg alg, cdc_params p, size_
     if (pl.sum != SUM_NONE && (s = grow(&h->ssup, &h->ssup_cap, len / 4096 + 66, false, 0)) != CDC_OK) return s;
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, 0)) != CDC_OK) return s;
     if ((s = grow(&h->hash, &h->hash_cap, items * seg_hash_bytes(), false, 0)) != CDC_OK) return s;
-    if ((s = grow(&h->plog, &h->plog_cap, items * seg_log_bytes(), false, 0)) != CDC_OK) return s;
+    if ((s = grow(&h->plog, &h->plog_cap, items * seg_log_bytes(kLogCap), false, 0)) != CDC_OK) return s;
     if ((s = grow(&h->groups, &h->groups_cap, ((items + GS - 1) / GS + 1) * group_state_bytes(), false, 0)) !=
         CDC_OK)
         return s;
@@ -750,10 +752,11 @@ constexpr uint64_t kFixBlocks = ((kFixMaxLen + 63 + 63) / 64 + 15) & ~15ull;
 constexpr uint64_t kFixSumBytes = round256(kFixBlocks + 64);
 constexpr uint64_t kFixSupBytes = round256((kFixMaxLen + 63 + 4095) / 4096 + 64);
 constexpr uint64_t kFixItems = kFixMaxLen / kFixMinSeg + 1;
-constexpr uint64_t kFixSegSlot = 3584;    // >= sizeof(SegState), checked at set-up
+constexpr uint64_t kFixSegSlot = 4096;    // >= sizeof(SegState), checked at set-up
 constexpr uint64_t kFixGroupSlot = 2048;  // >= sizeof(GroupState), checked at set-up
 constexpr uint64_t kFixHashSlot = 16384;  // >= a segment's position hash, checked at set-up
-constexpr uint64_t kFixLogSlot = 16384;   // >= a segment's step log, checked at set-up
+constexpr uint32_t kFixLogCap = 1024;     // speculation steps logged per segment
+constexpr uint64_t kFixLogSlot = 20480;   // >= a segment's step logs, checked at set-up
 constexpr uint64_t kFixGroups = kFixItems / GS + 2;
 constexpr uint64_t kFixCtrlBytes = 512;
 constexpr uint64_t kFixOffSmax = kFixCtrlBytes;
@@ -782,7 +785,7 @@ static cdc_status fixed_scratch(int dev, cudaStream_t st, uint8_t** out) {
     std::lock_guard<std::mutex> lock(g_fixed_mu);
     if (!g_fixed_ptr[dev]) {
         if (seg_state_bytes() > kFixSegSlot || group_state_bytes() > kFixGroupSlot ||
-            seg_hash_bytes() > kFixHashSlot || seg_log_bytes() > kFixLogSlot)
+            seg_hash_bytes() > kFixHashSlot || seg_log_bytes(kFixLogCap) > kFixLogSlot)
             return CDC_ERR_INTERNAL;
         uint8_t* p = nullptr;
         if (cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_fixed_scratch) != cudaSuccess || !p) {
@@ -873,6 +876,7 @@ extern "C" cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t*
     c.st = reinterpret_cast<SegState*>(scr + kFixOffSt);
     c.hash = reinterpret_cast<unsigned long long*>(scr + kFixOffHash);
     c.plog = reinterpret_cast<unsigned long long*>(scr + kFixOffLog);
+    c.logcap = kFixLogCap;
     c.groups = scr + kFixOffGroups;
     c.ctrl = ctrl;
     c.timeout_ns = timeout_ns;

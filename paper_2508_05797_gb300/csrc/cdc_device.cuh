@@ -20,7 +20,7 @@ struct Ctrl {
     unsigned int err;            // sticky error bits, cleared by the host
     unsigned int stats_on;       // 1: kernels accumulate the counters below
     unsigned int pad[5];
-    unsigned long long stats[24];  // see STAT_* (reset by the host)
+    unsigned long long stats[25];  // see STAT_* (reset by the host)
 };
 enum : int {
     STAT_SEGMENTS = 0,      // non-empty segments speculated
@@ -47,7 +47,8 @@ enum : int {
     STAT_OUT_PASSES = 21,   // passes of the output kernel over a step log
     STAT_OUT_RECS = 22,     // step-log records the output kernel replayed
     STAT_CYC_OUTPUT = 23,   // cycles of the output kernel, summed over segments
-    STAT_N = 24
+    STAT_CYC_OUT_STEPS = 24, //   of which in its own chain steps (staging included)
+    STAT_N = 25
 };
 enum : unsigned int { ERR_TIMEOUT = 1u, ERR_INTERNAL = 2u };
 

@@ -63,7 +63,8 @@ struct ChainLaunch {
     // workspace
     SegState* st;
     unsigned long long* hash;  // per segment: its position hash (seg_hash_bytes())
-    unsigned long long* plog;  // per segment: its step log (seg_log_bytes())
+    unsigned long long* plog;  // per segment: its step logs (seg_log_bytes(logcap))
+    uint32_t logcap;           // speculation-log records per segment
     void* groups;            // GroupState per GS segments
     Ctrl* ctrl;
     uint64_t timeout_ns;
@@ -105,7 +106,9 @@ int chain_smem(int rule, uint32_t win);
 int spec_blocks_per_sm(int rule, uint32_t win);
 size_t seg_state_bytes();
 size_t seg_hash_bytes();
-size_t seg_log_bytes();
+size_t seg_log_bytes(uint32_t logcap);
+// speculation steps a handle logs per segment (a segment with more is output by stepping)
+constexpr uint32_t HANDLE_LOG_CAP = 2048;
 size_t group_state_bytes();
 // ev_spec (may be null) is recorded on `st` right after the speculation kernel
 cudaError_t launch_chain(const ChainLaunch& a, int rule, const ChainGrids& g, cudaStream_t st, int* launches,

@@ -60,14 +60,19 @@ struct __align__(128) SegState {
     unsigned long long seg_lo, seg_hi, flo, fhi;
     unsigned int geo;                 // bit0 first of file, bit1 last of file, bit2 empty
     unsigned int flagA;               // X, counts, geometry, hash and step log published
-    unsigned int log_n;               // records in the step log (> LOGCAP: it overflowed)
+    unsigned int log_n;               // records in the step log (> logcap: it overflowed)
     unsigned int ures_n;              // entries of ures_* below
     // positions that reach this segment off every chain (the nearest non-empty
     // predecessor's uncovered exits), each followed here like a stitch walk
     unsigned long long ures_pos[NU];
     unsigned long long ures_exit[NU]; // exit when that walk met no chain either
     unsigned int ures_val[NU];        // table encoding of the walk's result
+    // written by k_stitch: where the walk from predecessor exit j is logged
+    // (records logcap + sw_first[j] .. + sw_cnt[j]; sw_cnt 0xFFFF: not logged)
+    unsigned short sw_first[NL];
+    unsigned short sw_cnt[NL];
     // written by k_settle
+    unsigned int entry_slot;          // predecessor chain the true path entered by, or NONE
     unsigned long long entry_pos;     // first true position >= seg_lo (or >= seg_hi)
     unsigned long long excl;          // boundaries before this segment
     unsigned int count;               // boundaries inside this segment
@@ -200,17 +205,20 @@ size_t seg_hash_bytes() { return (size_t)HSLOTS * sizeof(unsigned long long); }
 // position + d, ..., position + (k - 1) d, and goes on at position + k d.
 // A chain's records appear in increasing position order. The output kernel
 // replays the true chain from these records instead of stepping again.
-constexpr int LOGCAP = 1024;
-size_t seg_log_bytes() { return (size_t)LOGCAP * 16; }
+// (A.logcap records per segment, set by the host)
+// then the stitch walks: SWPW records per warp of the stitch kernel
+constexpr int SWPW = 64;
+constexpr int SWCAP = SWPW * (NL / 32);
+size_t seg_log_bytes(uint32_t logcap) { return (size_t)(logcap + SWCAP) * 16; }
 
 __device__ __forceinline__ void log_step(const ChainLaunch& A, uint64_t item, unsigned int* log_n, uint32_t chain,
                                          uint64_t pos, uint32_t k, uint64_t d) {
     const unsigned int i = atomicAdd(log_n, 1u);
-    if (i < (unsigned)LOGCAP) {
+    if (i < A.logcap) {
         ulonglong2 r;
         r.x = pos | ((unsigned long long)chain << 57);
         r.y = ((unsigned long long)k << 32) | (uint32_t)d;
-        reinterpret_cast<ulonglong2*>(A.plog)[item * (uint64_t)LOGCAP + i] = r;
+        reinterpret_cast<ulonglong2*>(A.plog)[item * (uint64_t)(A.logcap + SWCAP) + i] = r;
     }
 }
 
@@ -577,7 +585,8 @@ template <int RULE>
 __device__ uint32_t stitch_walk(const ChainLaunch& A, const SumView& S, const RawView& R, const Prm& P,
                                 const unsigned long long* ht, const unsigned long long* X, const unsigned int* cnt,
                                 uint64_t seg_lo, uint64_t seg_hi, uint64_t wflo, uint64_t fhi, bool last, uint64_t e,
-                                uint64_t* ux, uint64_t item) {
+                                uint64_t* ux, uint64_t item, ulonglong2* slog = nullptr, uint32_t* slog_n = nullptr,
+                                uint32_t slog_cap = 0) {
     const int lane = threadIdx.x & 31;
     uint32_t nsteps = 0;
     uint64_t v = e;
@@ -591,7 +600,14 @@ __device__ uint32_t stitch_walk(const ChainLaunch& A, const SumView& S, const Ra
         }
         uint32_t k;
         uint64_t dd;
+        const uint64_t v0 = v;
         v = w_advance<RULE>(S, R, P, wflo, fhi, v, seg_hi, &k, &dd);
+        // the step goes to the walk's log (same record format as the speculation log)
+        if (slog) {
+            if (lane == 0 && *slog_n < slog_cap)
+                slog[*slog_n] = make_ulonglong2(v0, ((unsigned long long)k << 32) | (uint32_t)dd);
+            (*slog_n)++;
+        }
         ne += k;
         nsteps++;
         if (lane == 0) stat_add(A, STAT_STITCH_STEPS, 1);
@@ -672,6 +688,7 @@ __global__ void __launch_bounds__(NL) k_stitch(ChainLaunch A) {
         const bool first = geo & GEO_FIRST, last = geo & GEO_LAST, empty = geo & GEO_EMPTY;
         uint32_t tab;
         unsigned long long unk = ~0ull;  // no position: slots of chains that never ran stay so
+        unsigned short swf = 0, swc = 0xFFFFu;  // this slot's logged walk
         if (first) {
             tab = stab_enc(0, me->cnt[0] - 1 + (last ? 1u : 0u)) | STAB_CONST;
         } else if (empty) {
@@ -685,22 +702,31 @@ __global__ void __launch_bounds__(NL) k_stitch(ChainLaunch A) {
             const uint64_t seg_lo = me->seg_lo, seg_hi = me->seg_hi, flo = me->flo, fhi = me->fhi;
             tab = STAB_UNKNOWN;
             uint32_t todo = __ballot_sync(FULL, xp != ~0ull);
+            // this warp's walks go to its part of the segment's stitch log
+            ulonglong2* slog = reinterpret_cast<ulonglong2*>(A.plog) + item * (uint64_t)(A.logcap + SWCAP) + A.logcap +
+                               (uint64_t)(tid >> 5) * SWPW;
+            uint32_t slog_n = 0;
             while (todo) {
                 const int ld = __ffs((int)todo) - 1;
                 const uint64_t e = __shfl_sync(FULL, xp, ld);
                 const uint32_t same = __ballot_sync(FULL, xp == e) & todo;
                 uint64_t ux;
+                const uint32_t first_rec = slog_n;
                 const uint32_t res = stitch_walk<RULE>(A, S, R, P, sh.ht, sh.X, sh.cnt, seg_lo, seg_hi, flo - A.wctx, fhi,
-                                                       last, e, &ux, item);
+                                                       last, e, &ux, item, slog, &slog_n, SWPW);
                 if ((same >> lane) & 1u) {
                     tab = res;
                     unk = ux;
+                    swf = (unsigned short)((tid >> 5) * SWPW + first_rec);
+                    swc = slog_n <= (uint32_t)SWPW ? (unsigned short)(slog_n - first_rec) : (unsigned short)0xFFFFu;
                 }
                 todo &= ~same;
             }
         }
         me->table[tid] = tab;
         me->unk_exit[tid] = unk;
+        me->sw_first[tid] = swf;
+        me->sw_cnt[tid] = swc;
         __syncthreads();
         if (A.stats && tid == 0) stat_add(A, STAT_CYC_STITCH, (unsigned long long)(clock64() - t0));
     }
@@ -1077,6 +1103,7 @@ __global__ void __launch_bounds__(32) k_settle(ChainLaunch A) {
                 uint64_t entry = st->flo;
                 if (!(geo & GEO_FIRST)) entry = my_slot < NL ? A.st[i - 1].X[my_slot] : my_pos;
                 st->entry_pos = entry;
+                st->entry_slot = !(geo & GEO_FIRST) && my_slot < NL ? my_slot : NONE;
                 st->excl = my_excl;
                 st->count = my_cnt;
             }
@@ -1121,6 +1148,7 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
         };
         // one step the ordinary way (positions not on a logged chain)
         auto step = [&]() {
+            const long long t_step = A.stats ? clock64() : 0;
             if (!staged) {
                 uint64_t wb0 = (seg_lo >> 6) & ~15ull;
                 uint64_t wn = A.win;
@@ -1161,13 +1189,36 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
                 if (p != flo) emit(p - flo);
             }
             v = e;
+            if (A.stats && lane == 0) stat_add(A, STAT_CYC_OUT_STEPS, (unsigned long long)(clock64() - t_step));
         };
         const long long t_seg = clock64();
         if (!(geo & GEO_EMPTY)) {
+            // the stitch kernel's walk from the entry, if it was logged: its
+            // records run from the entry to the first speculated position
+            const uint32_t es = first ? NONE : st->entry_slot;
+            if (es < (uint32_t)NL && st->sw_cnt[es] != 0xFFFFu) {
+                const uint32_t c = st->sw_cnt[es];
+                const ulonglong2* sl = reinterpret_cast<const ulonglong2*>(A.plog) +
+                                       item * (uint64_t)(A.logcap + SWCAP) + A.logcap + st->sw_first[es];
+                static_assert(SWPW <= 64, "two records per lane");
+                ulonglong2 r0 = make_ulonglong2(0, 0), r1 = make_ulonglong2(0, 0);
+                if ((uint32_t)lane < c) r0 = sl[lane];
+                if ((uint32_t)lane + 32 < c) r1 = sl[lane + 32];
+                for (uint32_t i = 0; i < c; i++) {
+                    const uint64_t p = __shfl_sync(FULL, i < 32 ? r0.x : r1.x, i & 31);
+                    const uint64_t kd = __shfl_sync(FULL, i < 32 ? r0.y : r1.y, i & 31);
+                    if (p != v) break;  // not the path from the entry: leave the rest to the loop below
+                    const uint32_t k = (uint32_t)(kd >> 32);
+                    const uint64_t d = (uint32_t)kd;
+                    if (lane == 0) stat_add(A, STAT_OUT_RECS, 1);
+                    for (uint32_t j = 0; j < k; j++) emit(v + j * d - flo);
+                    v += (uint64_t)k * d;
+                }
+            }
             const uint32_t ln = st->log_n;
-            const bool use_log = ln <= (uint32_t)LOGCAP;
+            const bool use_log = ln <= A.logcap;
             const unsigned long long* ht = A.hash + item * (uint64_t)HSLOTS;
-            const ulonglong2* lg = reinterpret_cast<const ulonglong2*>(A.plog) + item * (uint64_t)LOGCAP;
+            const ulonglong2* lg = reinterpret_cast<const ulonglong2*>(A.plog) + item * (uint64_t)(A.logcap + SWCAP);
             constexpr uint64_t POS = (1ull << 57) - 1;
             while (v < seg_hi) {
                 // the chain whose recorded path holds v (the first segment of a

@@ -242,7 +242,7 @@ static size_t workspace_bytes(size_t arena, size_t nf, int sms) {
     const size_t items = arena / seg + nf + 2;
     const size_t nblk = (arena + 127) / 64 + 16;
     size_t b = 2 * (nblk + 64) + arena / 4096 + 66;
-    b += items * (cdc::seg_state_bytes() + cdc::seg_hash_bytes() + cdc::seg_log_bytes());
+    b += items * (cdc::seg_state_bytes() + cdc::seg_hash_bytes() + cdc::seg_log_bytes(cdc::HANDLE_LOG_CAP));
     b += ((items + 127) / 128 + 1) * cdc::group_state_bytes();
     b += (nf + 1) * 8 + cdc::batch_scan_tmp_elems(nf) * 8 + items * 4 + 4096;
     return b + b / 4 + 8 * 64 * 4;
