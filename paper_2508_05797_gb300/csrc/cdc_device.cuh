@@ -47,7 +47,7 @@ enum : int {
     STAT_OUT_PASSES = 21,   // passes of the output kernel over a step log
     STAT_OUT_RECS = 22,     // step-log records the output kernel replayed
     STAT_CYC_OUTPUT = 23,   // cycles of the output kernel, summed over segments
-    STAT_CYC_OUT_STEPS = 24, //   of which in its own chain steps (staging included)
+    STAT_CYC_OUT_STEPS = 24, //   of which in its own chain steps
     STAT_N = 25
 };
 enum : unsigned int { ERR_TIMEOUT = 1u, ERR_INTERNAL = 2u };

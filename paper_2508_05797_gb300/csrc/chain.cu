@@ -30,9 +30,10 @@
 //            exact), settling entries no table covers by following the chain.
 //  k_settle  (one warp per group): carries the state through the group's
 //            segments; records each segment's true entry and global offset.
-//  k_output  (one warp per segment): replays the true chain from the step log
-//            (the hash names the chain at a position), stepping only where no
-//            record covers it, and writes its boundaries at that offset.
+//  k_output  (one warp per segment): replays the true chain from the logs (the
+//            stitch walk from its entry, then the speculation log, where the
+//            hash names the chain at a position), stepping only where no record
+//            covers it, and writes its boundaries at that offset.
 // Every wait (a segment on its predecessor's speculation) is bounded.
 #include "cdc_device.cuh"
 #include "cdc_launch.h"
@@ -1117,7 +1118,6 @@ __global__ void __launch_bounds__(32) k_settle(ChainLaunch A) {
 template <int RULE>
 __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
     if (ld_volatile(&A.ctrl->err)) return;  // a speculation wait ran out: nothing to resolve
-    extern __shared__ __align__(16) uint8_t dsm[];
     const int lane = threadIdx.x;
     const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
                                            : A.n_items;
@@ -1130,10 +1130,8 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
         const uint64_t excl = st->excl;
         const uint32_t cnt = st->count;
         const bool first = geo & GEO_FIRST, last = geo & GEO_LAST;
-        // summaries of the segment's window, staged on the first ordinary step
-        SumView S{A.smax, A.sarg, dsm, dsm + A.win, 0, 0, A.ssup};
-        Win W{dsm, dsm + A.win, 0, 0};
-        bool staged = !(RULE == RULE_RAM || RULE == RULE_AE || RULE == RULE_MAXP);
+        // (rare) ordinary steps read the summaries from global memory
+        const SumView S{A.smax, A.sarg, nullptr, nullptr, 0, 0, A.ssup};
         uint64_t v = first ? flo : st->entry_pos;
         uint64_t kb = excl, held = 0;
         uint32_t nb = 0;
@@ -1149,40 +1147,9 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
         // one step the ordinary way (positions not on a logged chain)
         auto step = [&]() {
             const long long t_step = A.stats ? clock64() : 0;
-            if (!staged) {
-                uint64_t wb0 = (seg_lo >> 6) & ~15ull;
-                uint64_t wn = A.win;
-                if (wb0 + wn > A.nblk_pad) wn = A.nblk_pad > wb0 ? ((A.nblk_pad - wb0) & ~15ull) : 0;
-                constexpr int US = 4;  // 16-byte loads in flight per lane and array
-                for (uint64_t o0 = (uint64_t)lane * 16; o0 < wn; o0 += 512 * US) {
-                    uint4 m[US], a[US];
-#pragma unroll
-                    for (int u = 0; u < US; u++) {
-                        const uint64_t o = o0 + 512 * u;
-                        if (o < wn) {
-                            m[u] = *reinterpret_cast<const uint4*>(A.smax + wb0 + o);
-                            if (RULE != RULE_MAXP) a[u] = *reinterpret_cast<const uint4*>(A.sarg + wb0 + o);
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < US; u++) {
-                        const uint64_t o = o0 + 512 * u;
-                        if (o < wn) {
-                            *reinterpret_cast<uint4*>(dsm + o) = m[u];
-                            if (RULE != RULE_MAXP) *reinterpret_cast<uint4*>(dsm + A.win + o) = a[u];
-                        }
-                    }
-                }
-                S.wb0 = wb0;
-                S.wn = wn;
-                W.p0 = wb0 << 6;
-                W.nb = (uint32_t)(wn << 6);
-                staged = true;
-                __syncwarp();
-            }
             uint32_t k;
             uint64_t dd;
-            const uint64_t e = f_advance<RULE>(W, S, R, P, flo - A.wctx, fhi, v, seg_hi, &k, &dd);
+            const uint64_t e = w_advance<RULE>(S, R, P, flo - A.wctx, fhi, v, seg_hi, &k, &dd);
             if (lane == 0) stat_add(A, STAT_OUT_STEPS, 1);
             for (uint32_t i = 0; i < k; i++) {
                 const uint64_t p = v + i * dd;
@@ -1345,7 +1312,7 @@ template <int RULE>
 int allow_smem() {
     return launch_memo(100 + RULE, 0, [](uint32_t) {
         int e = allow_max_smem(k_spec<RULE>);
-        return e == (int)cudaSuccess ? allow_max_smem(k_output<RULE>) : e;
+        return e;
     });
 }
 
@@ -1362,7 +1329,7 @@ static cudaError_t launch_rule(const ChainLaunch& a, const ChainGrids& gr, cudaS
     k_compose<RULE><<<gr.groups, 32, 0, st>>>(a);
     k_scan<RULE><<<1, 32, 0, st>>>(a);
     k_settle<RULE><<<gr.groups, 32, 0, st>>>(a);
-    k_output<RULE><<<gr.output, 32, sm, st>>>(a);
+    k_output<RULE><<<gr.output, 32, 0, st>>>(a);
     *launches += 7;
     return cudaGetLastError();
 }
