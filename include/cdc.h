@@ -252,7 +252,7 @@ CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
  *     wrong results. Serialise them.
  */
 #define CDC_STATIC_MAX_LEN ((size_t)16 << 20)
-#define CDC_STATIC_SCRATCH_BYTES ((size_t)21554432)
+#define CDC_STATIC_SCRATCH_BYTES ((size_t)21677312)
 
 CDC_API cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
                                     uint64_t* out_bounds, size_t* n, cdc_stream stream);

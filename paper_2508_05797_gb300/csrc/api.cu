@@ -281,6 +281,18 @@ static uint32_t pick_starts(cdc_handle h, uint64_t span) {
     return (uint32_t)n;
 }
 
+// segments per group of the table scan. The group kernels walk a group's
+// segments one after another and the scan walks the groups one after another,
+// so the latency is about gs * (compose + settle step) + (items / gs) * (scan
+// step); with the scan step about a fifth of the other two, the smallest power
+// of two >= sqrt(items) / 2 is near the optimum (16 for a 16 MiB input, 64 for
+// 4 GiB), within GS_MIN..GS_MAX. Results do not depend on it.
+static uint32_t pick_gs(uint64_t items) {
+    uint32_t g = GS_MIN;
+    while (g < (uint32_t)GS_MAX && 4ull * g * g < items) g *= 2;
+    return g;
+}
+
 static uint64_t pick_span(cdc_handle h, cdc_params p, uint64_t seg) {
     uint64_t sp = h->span ? (uint64_t)h->span : (uint64_t)p.max / 8;
     if (sp < 32) sp = 32;
@@ -340,8 +352,8 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, st)) != CDC_OK) return s;
     if ((s = grow(&h->hash, &h->hash_cap, items * seg_hash_bytes(), false, st)) != CDC_OK) return s;
     if ((s = grow(&h->plog, &h->plog_cap, items * seg_log_bytes(kLogCap), false, st)) != CDC_OK) return s;
-    if ((s = grow(&h->groups, &h->groups_cap, ((items + GS - 1) / GS + 1) * group_state_bytes(), false, st)) !=
-        CDC_OK)
+    if ((s = grow(&h->groups, &h->groups_cap, ((items + GS_MIN - 1) / GS_MIN + 1) * group_state_bytes(), false,
+                  st)) != CDC_OK)
         return s;
     if (batch) {
         if ((s = grow(&h->item_off, &h->files_cap, n_files + 1, false, st)) != CDC_OK) return s;
@@ -420,6 +432,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     c.stats = (int)h->stats;
     c.warp_chains = h->warp_chains ? (uint32_t)h->warp_chains : 96u;
     c.starts = pick_starts(h, c.span);
+    c.gs = pick_gs(items);
     if (h->stats) cudaMemsetAsync(h->ctrl->stats, 0, sizeof(h->ctrl->stats), st);
     if (pl.sum != SUM_NONE) {
         const uint64_t mx4k = ((uint64_t)p.max + 4095) & ~4095ull;
@@ -429,7 +442,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
         c.adj_cap = 64ull << 20;
     }
     ChainGrids gr;
-    const uint64_t ngroups = (items + GS - 1) / GS;
+    const uint64_t ngroups = (items + c.gs - 1) / c.gs;
     uint64_t gs = (uint64_t)h->sm_count * spec_blocks_per_sm(pl.rule, c.win);
     gr.spec = (int)(gs < items ? gs : items);
     gr.stitch = (int)(items < (uint64_t)h->sm_count * 8 ? items : (uint64_t)h->sm_count * 8);
@@ -665,8 +678,8 @@ extern "C" cdc_status cdc_reserve(cdc_handle h, cdc_alg alg, cdc_params p, size_
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, 0)) != CDC_OK) return s;
     if ((s = grow(&h->hash, &h->hash_cap, items * seg_hash_bytes(), false, 0)) != CDC_OK) return s;
     if ((s = grow(&h->plog, &h->plog_cap, items * seg_log_bytes(kLogCap), false, 0)) != CDC_OK) return s;
-    if ((s = grow(&h->groups, &h->groups_cap, ((items + GS - 1) / GS + 1) * group_state_bytes(), false, 0)) !=
-        CDC_OK)
+    if ((s = grow(&h->groups, &h->groups_cap, ((items + GS_MIN - 1) / GS_MIN + 1) * group_state_bytes(), false,
+                  0)) != CDC_OK)
         return s;
     if (n_files) {
         if ((s = grow(&h->item_off, &h->files_cap, n_files + 1, false, 0)) != CDC_OK) return s;
@@ -757,7 +770,7 @@ constexpr uint64_t kFixGroupSlot = 2048;  // >= sizeof(GroupState), checked at s
 constexpr uint64_t kFixHashSlot = 16384;  // >= a segment's position hash, checked at set-up
 constexpr uint32_t kFixLogCap = 1024;     // speculation steps logged per segment
 constexpr uint64_t kFixLogSlot = 20480;   // >= a segment's step logs, checked at set-up
-constexpr uint64_t kFixGroups = kFixItems / GS + 2;
+constexpr uint64_t kFixGroups = kFixItems / GS_MIN + 2;
 constexpr uint64_t kFixCtrlBytes = 512;
 constexpr uint64_t kFixOffSmax = kFixCtrlBytes;
 constexpr uint64_t kFixOffSarg = kFixOffSmax + kFixSumBytes;
@@ -882,6 +895,7 @@ extern "C" cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t*
     c.timeout_ns = timeout_ns;
     c.hold_item = -1;
     c.warp_chains = 96u;
+    c.gs = pick_gs(items);
     if (pl.sum != SUM_NONE) {
         const uint64_t mx4k = ((uint64_t)p.max + 4095) & ~4095ull;
         c.quiet_run = pl.sum == SUM_MAXP ? (uint32_t)(p.max / 8192 > 1 ? p.max / 8192 : 1) : 1u;
@@ -890,7 +904,7 @@ extern "C" cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t*
         c.adj_cap = 64ull << 20;
     }
     ChainGrids gr;
-    const uint64_t ngroups = (items + GS - 1) / GS;
+    const uint64_t ngroups = (items + c.gs - 1) / c.gs;
     const uint64_t gs = (uint64_t)cfg.sm_count * spec_blocks_per_sm(pl.rule, c.win);
     gr.spec = (int)(gs < items ? gs : items);
     gr.stitch = (int)(items < (uint64_t)cfg.sm_count * 8 ? items : (uint64_t)cfg.sm_count * 8);

@@ -55,7 +55,10 @@ enum : unsigned int { ERR_TIMEOUT = 1u, ERR_INTERNAL = 2u };
 // Speculation geometry of the chain stage.
 constexpr int NW = 4;            // warps per segment
 constexpr int NL = 32 * NW;      // speculative chains per segment
-constexpr int GS = 128;          // segments per group in the table scan
+// Segments per group in the table scan: chosen per call between these bounds
+// (group walks are serial within a group, the scan is serial across groups)
+constexpr int GS_MIN = 8;
+constexpr int GS_MAX = 128;
 
 #if defined(__CUDACC__)
 

@@ -65,13 +65,14 @@ struct ChainLaunch {
     unsigned long long* hash;  // per segment: its position hash (seg_hash_bytes())
     unsigned long long* plog;  // per segment: its step logs (seg_log_bytes(logcap))
     uint32_t logcap;           // speculation-log records per segment
-    void* groups;            // GroupState per GS segments
+    void* groups;            // GroupState per group of gs segments
     Ctrl* ctrl;
     uint64_t timeout_ns;
     int64_t hold_item;
     int stats;               // accumulate Ctrl::stats
     uint32_t warp_chains;    // per-thread speculation rounds run while more chains than this are alive
     uint32_t starts;         // distinct speculative starts per segment (threads beyond repeat them)
+    uint32_t gs;             // segments per group of the table scan (GS_MIN..GS_MAX)
 };
 
 // Memo of per-device launch properties: fn(arg) runs once per (device, key, arg).

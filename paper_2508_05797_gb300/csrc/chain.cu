@@ -24,7 +24,8 @@
 //            exit until it lands on a hashed position (or ends on a chain's
 //            exit). Result: predecessor chain -> (chain, boundaries in segment).
 //  k_ures    follows the few exits no chain covers into the next segment.
-//  k_compose (one warp per group of GS segments): composes the group's tables.
+//  k_compose (one warp per group of A.gs segments, 8..128 chosen per call):
+//            composes the group's tables.
 //  k_scan    (one warp): carries the true state across the group composites
 //            from the start of the data (the first segment of every file is
 //            exact), settling entries no table covers by following the chain.
@@ -902,9 +903,9 @@ __global__ void __launch_bounds__(32) k_compose(ChainLaunch A) {
     const int lane = threadIdx.x;
     const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
                                            : A.n_items;
-    const uint64_t ngroups = (n_items + GS - 1) / GS;
+    const uint64_t ngroups = (n_items + A.gs - 1) / A.gs;
     for (uint64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        const uint64_t i0 = g * GS, i1 = umin64(i0 + GS, n_items);
+        const uint64_t i0 = g * A.gs, i1 = umin64(i0 + A.gs, n_items);
         uint32_t sl[4];
         unsigned long long cn[4], ps[4];  // ps: position while sl == NONE (off every chain)
 #pragma unroll
@@ -979,7 +980,7 @@ __global__ void __launch_bounds__(32) k_scan(ChainLaunch A) {
     const int lane = threadIdx.x;
     const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
                                            : A.n_items;
-    const uint64_t ngroups = (n_items + GS - 1) / GS;
+    const uint64_t ngroups = (n_items + A.gs - 1) / A.gs;
     GroupState* G = reinterpret_cast<GroupState*>(A.groups);
     uint32_t slot = NONE;
     uint64_t pos = A.lo, incl = 0;
@@ -996,7 +997,7 @@ __global__ void __launch_bounds__(32) k_scan(ChainLaunch A) {
                     gsl[b][j] = G[g].slot[lane + 32 * j];
                     gcn[b][j] = G[g].count[lane + 32 * j];
                 }
-                gfirst[b] = A.st[g * GS].geo & GEO_FIRST;
+                gfirst[b] = A.st[g * A.gs].geo & GEO_FIRST;
             }
         }
 #pragma unroll
@@ -1024,7 +1025,7 @@ __global__ void __launch_bounds__(32) k_scan(ChainLaunch A) {
                 incl += nc;
             } else {
                 // follow the group segment by segment (tables prefetched one ahead)
-                const uint64_t i0 = g * GS, i1 = umin64(i0 + GS, n_items);
+                const uint64_t i0 = g * A.gs, i1 = umin64(i0 + A.gs, n_items);
                 uint32_t nt[4];
 #pragma unroll
                 for (int j = 0; j < 4; j++) nt[j] = A.st[i0].table[lane + 32 * j];
@@ -1056,12 +1057,12 @@ __global__ void __launch_bounds__(32) k_settle(ChainLaunch A) {
     const int lane = threadIdx.x;
     const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
                                            : A.n_items;
-    const uint64_t ngroups = (n_items + GS - 1) / GS;
+    const uint64_t ngroups = (n_items + A.gs - 1) / A.gs;
     const GroupState* G = reinterpret_cast<const GroupState*>(A.groups);
     for (uint64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
         uint32_t slot = G[g].entry_slot;
         uint64_t pos = G[g].entry_pos, incl = G[g].entry_incl;
-        const uint64_t i0 = g * GS, i1 = umin64(i0 + GS, n_items);
+        const uint64_t i0 = g * A.gs, i1 = umin64(i0 + A.gs, n_items);
         for (uint64_t b0 = i0; b0 < i1; b0 += 32) {
             // lane t records segment b0 + t: the state before it, its offset and count
             uint32_t my_slot = NONE, my_cnt = 0;
