@@ -163,7 +163,8 @@ typedef enum {
                                  each step); 1..128, 0 = automatic (96) */
     CDC_OPT_STARTS = 8        /* distinct speculative starts per segment, spread
                                  over its first `span` bytes; 1..128, 0 =
-                                 automatic (span / 128, within 16..128) */
+                                 automatic (span / 128, within 16..128;
+                                 16 for MAXP) */
 } cdc_option;
 
 CDC_API cdc_status cdc_set_option(cdc_handle h, cdc_option opt, int64_t value);

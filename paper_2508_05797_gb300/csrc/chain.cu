@@ -853,12 +853,14 @@ __device__ __forceinline__ uint32_t lookup(uint32_t t0, const uint32_t t[NL / 32
 }
 
 // One step of the true state through segment i, given its table entry e for
-// the state. (slot, pos): chain of the previous segment, or NONE and the
-// exact position. Returns the boundaries inside segment i.
+// the state and its geometry word geo. (slot, pos): chain of the previous
+// segment, or NONE and the exact position. Returns the boundaries inside
+// segment i.
 template <int RULE>
-__device__ uint32_t step_with(const ChainLaunch& A, uint64_t i, uint32_t e, uint32_t* slot, uint64_t* pos) {
+__device__ uint32_t step_with(const ChainLaunch& A, uint64_t i, uint32_t e, uint32_t geo, uint32_t* slot,
+                              uint64_t* pos) {
     const SegState* st = &A.st[i];
-    if (st->geo & GEO_EMPTY) return 0;  // nothing inside: the state passes through
+    if (geo & GEO_EMPTY) return 0;  // nothing inside: the state passes through
     if (!(e & STAB_UNKNOWN) || (e & STAB_CONST)) {
         *slot = stab_slot(e);
         *pos = 0;
@@ -911,7 +913,7 @@ __global__ void __launch_bounds__(32) k_compose(ChainLaunch A) {
 #pragma unroll
         for (int j = 0; j < 4; j++) { sl[j] = (uint32_t)(lane + 32 * j); cn[j] = 0; ps[j] = 0; }
         // tables of the next PD segments in flight (slot d holds segment i with (i - i0) % PD == d)
-        constexpr uint64_t PD = 4;
+        constexpr uint64_t PD = 8;
         uint32_t nt[PD][4], ngeo[PD];
 #pragma unroll
         for (uint64_t d = 0; d < PD; d++)
@@ -1026,19 +1028,21 @@ __global__ void __launch_bounds__(32) k_scan(ChainLaunch A) {
             } else {
                 // follow the group segment by segment (tables prefetched one ahead)
                 const uint64_t i0 = g * A.gs, i1 = umin64(i0 + A.gs, n_items);
-                uint32_t nt[4];
+                uint32_t nt[4], ng = A.st[i0].geo;
 #pragma unroll
                 for (int j = 0; j < 4; j++) nt[j] = A.st[i0].table[lane + 32 * j];
                 for (uint64_t i = i0; i < i1; i++) {
                     uint32_t t[4];
+                    const uint32_t geo = ng;
 #pragma unroll
                     for (int j = 0; j < 4; j++) t[j] = nt[j];
                     if (i + 1 < i1) {
 #pragma unroll
                         for (int j = 0; j < 4; j++) nt[j] = A.st[i + 1].table[lane + 32 * j];
+                        ng = A.st[i + 1].geo;
                     }
                     const uint32_t e = lookup(t[0], t, slot);
-                    incl += step_with<RULE>(A, i, e, &slot, &pos);
+                    incl += step_with<RULE>(A, i, e, geo, &slot, &pos);
                 }
             }
         }
@@ -1068,14 +1072,16 @@ __global__ void __launch_bounds__(32) k_settle(ChainLaunch A) {
             uint32_t my_slot = NONE, my_cnt = 0;
             uint64_t my_pos = 0, my_excl = 0;
             const uint32_t nb = (uint32_t)umin64(32, i1 - b0);
-            // tables of the next PD segments in flight (slot d holds segment k with k % PD == d)
+            // tables and geometry words of the next PD segments in flight (slot d
+            // holds segment k with k % PD == d)
             constexpr uint32_t PD = 4;
-            uint32_t nt[PD][4];
+            uint32_t nt[PD][4], ngeo[PD];
 #pragma unroll
             for (uint32_t d = 0; d < PD; d++)
                 if (d < nb) {
 #pragma unroll
                     for (int j = 0; j < 4; j++) nt[d][j] = A.st[b0 + d].table[lane + 32 * j];
+                    ngeo[d] = A.st[b0 + d].geo;
                 }
             for (uint32_t k0 = 0; k0 < nb; k0 += PD) {
 #pragma unroll
@@ -1086,13 +1092,15 @@ __global__ void __launch_bounds__(32) k_settle(ChainLaunch A) {
                         uint32_t t[4];
 #pragma unroll
                         for (int j = 0; j < 4; j++) t[j] = nt[d][j];
+                        const uint32_t geo = ngeo[d];
                         if (k + PD < nb) {
 #pragma unroll
                             for (int j = 0; j < 4; j++) nt[d][j] = A.st[i + PD].table[lane + 32 * j];
+                            ngeo[d] = A.st[i + PD].geo;
                         }
                         if (lane == (int)k) { my_slot = slot; my_pos = pos; my_excl = incl; }
                         const uint32_t e = lookup(t[0], t, slot);
-                        const uint32_t n = step_with<RULE>(A, i, e, &slot, &pos);
+                        const uint32_t n = step_with<RULE>(A, i, e, geo, &slot, &pos);
                         incl += n;
                         if (lane == (int)k) my_cnt = n;
                     }
