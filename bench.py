@@ -455,6 +455,70 @@ def dedup_workload(dev, base_bytes: int = GIB, n_versions: int = 15, reps: int =
     return res
 
 
+def small_workload(dev, copies: int = 16, reps: int = 5):
+    """Single 16 MiB buffers of uniform bytes (seed 0) chunked with RAM, AE and
+    MAXP at 8 KiB mean (windows from the calibrated table). A call this small is
+    bound by the latency of its kernel sequence, not by HBM: 16 calls on 16
+    copies of the buffer (256 MiB, more than L2) are captured in one CUDA graph,
+    replayed, and the time per call is the replay time / 16."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2508_05797_gb300 import Chunker
+
+    n = 16 * MIB
+    t = wtable()["uniform_16m_seed0"]
+    buf = torch.from_numpy(synth.uniform(0, n)).to(dev)
+    ds = [buf.clone() for _ in range(copies)]
+    del buf
+    s = torch.cuda.Stream(dev)
+    res = {"workload": "uniform 16 MiB (seed 0), one call per buffer; %d calls on %d copies in one CUDA graph, "
+                       "time per call = replay time / %d" % (copies, copies, copies)}
+    peak, _ = peaks()
+    for alg in ALGS:
+        e = t[alg]["8192"]
+        w, mn, mx = e["w"], e["min"], e["max"]
+        ck = Chunker(dev.index)
+        ck.reserve(alg, w, mn, mx, n)
+        outs = [torch.empty(n // mn + 1, dtype=torch.int64, device=dev) for _ in range(copies)]
+        cnts = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(copies)]
+
+        def calls():
+            for d, o, c in zip(ds, outs, cnts):
+                ck.chunk_async(d, alg, w, mn, mx, o, c, stream=s)
+
+        with torch.cuda.stream(s):
+            calls()
+        s.synchronize()
+        ck.sync_status(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            calls()
+        ts = []
+        with torch.cuda.stream(s):
+            for r in range(reps + 2):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                g.replay()
+                b.record(s)
+                s.synchronize()
+                if r >= 2:
+                    ts.append(a.elapsed_time(b) / copies)
+        ck.sync_status(s)
+        counts = {int(c.item()) for c in cnts}
+        if len(counts) != 1:
+            raise RuntimeError("small workload: copies of one buffer gave different boundary counts")
+        ms = statistics.median(ts)
+        res[alg] = {"us_per_call": round(ms * 1e3, 1), "GBps": round(n / (ms / 1e3) / 1e9, 1),
+                    "hbm_frac": round(n / (ms / 1e3) / 1e9 / peak, 4), "boundaries": counts.pop(), "w": w}
+        del g
+        ck.close()
+    del ds
+    torch.cuda.empty_cache()
+    return res
+
+
 def stream_workload(data, dev, pieces_mib=(64, 256), reps: int = 2):
     """Resumable chunking (cdc_feed_*): the 4 GiB mixed stream handed over in
     device pieces of a fixed size, RAM and MAXP at 8 KiB mean; GB/s of stream
@@ -553,6 +617,7 @@ def main():
     ap.add_argument("--no-prims", action="store_true", help="skip the EBS / RS measurement")
     ap.add_argument("--no-dedup", action="store_true", help="skip the dedup-shaped versions measurement")
     ap.add_argument("--no-stream", action="store_true", help="skip the resumable-feed measurement")
+    ap.add_argument("--no-small", action="store_true", help="skip the 16 MiB single-buffer (latency) measurement")
     ap.add_argument("--streams", type=int, default=3, help="streams the nine calls of a step are spread over")
     ap.add_argument("--ref-sample-mib", type=int, default=32, help="reference arm: bytes per (alg, mean) pair")
     ap.add_argument("--serving-requests", type=int, default=20_000)
@@ -734,6 +799,8 @@ def main():
                        "steps": e2e_steps, "host_threads": nstreams,
                        "path": "cdc_chunk_host (pinned host bytes in, host boundaries out), one thread and "
                                "stream per group of calls"}
+    if rank == 0 and not args.no_small:
+        line["small"] = small_workload(dev)
     if rank == 0 and not args.no_stream:
         line["stream"] = stream_workload(data, dev)
     if rank == 0 and not args.no_dedup:

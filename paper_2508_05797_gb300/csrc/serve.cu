@@ -111,22 +111,26 @@ bool cdc_server_s::launch(Slot& s, std::deque<Request>& pending, double now) {
     const Request key = *first;
     s.batch.clear();
     size_t bytes = 0, nb = 0;
-    for (auto it = first; it != pending.end() && s.batch.size() < max_files;) {
-        if (it->t_arrive > now || !same_kind(*it, key)) {
-            ++it;
-            continue;
+    // one pass: the requests taken go to the batch, the others (in order) to
+    // `rest`, which becomes the pending queue (erasing from the middle of the
+    // queue instead would cost time quadratic in its length)
+    std::deque<Request> rest;
+    bool open = true;
+    for (auto it = pending.begin(); it != pending.end(); ++it) {
+        if (open && it >= first && it->t_arrive <= now && same_kind(*it, key)) {
+            const size_t need_b = it->len / it->p.min + 1;
+            if (bytes + it->len <= slot_bytes && nb + need_b <= s.bounds_cap) {
+                bytes += it->len;
+                nb += need_b;
+                s.batch.push_back(*it);
+                if (s.batch.size() >= max_files) open = false;
+                continue;
+            }
+            if (!s.batch.empty()) open = false;  // the batch is full (submit rejects requests larger than a slot)
         }
-        const size_t need_b = it->len / it->p.min + 1;
-        if (bytes + it->len > slot_bytes || nb + need_b > s.bounds_cap) {
-            if (s.batch.empty()) ++it;  // cannot happen: submit rejects larger requests
-            else break;
-            continue;
-        }
-        bytes += it->len;
-        nb += need_b;
-        s.batch.push_back(*it);
-        it = pending.erase(it);
+        rest.push_back(*it);
     }
+    pending.swap(rest);
     if (s.batch.empty()) return false;
     const size_t n = s.batch.size();
     s.h_off[0] = 0;
