@@ -255,18 +255,23 @@ static Plan make_plan(cdc_handle h, cdc_alg alg, cdc_params p) {
     return pl;
 }
 
-// segment size: a few segments per resident warp, 64-byte multiple. Longer
-// segments let more speculative chains join inside them; the cap keeps the
-// staged summary window (segment + bound room + max, two bytes per block for
-// RAM / AE, one for MAXP) small enough for five or six resident speculation
-// blocks per SM. Caps measured on the 4 GiB mixed stream: 384 KiB for RAM / AE
-// up to max = 64 KiB, 256 KiB above, 512 KiB for MAXP. Floors measured on
-// 16 MiB inputs: 32 KiB for RAM / AE, 64 KiB for MAXP (15% faster than 32 KiB).
+// segment size: a few segments per SM (four for RAM / AE, sixteen for MAXP),
+// 64-byte multiple. Longer segments let more speculative chains join inside
+// them; the cap keeps the staged summary window (segment + bound room + max,
+// two bytes per block for RAM / AE, one for MAXP) small enough for five or six
+// resident speculation blocks per SM. Caps measured on the 4 GiB mixed stream:
+// 384 KiB for RAM / AE up to max = 64 KiB, 256 KiB above, 512 KiB for MAXP.
+// Floors measured on 16 MiB inputs: 32 KiB for RAM / AE, 64 KiB for MAXP (15%
+// faster than 32 KiB). Four per SM rather than sixteen for RAM / AE: on the
+// mixed stream 1.45x (RAM) and 1.24x (AE) faster at 64 MiB, 1.18x at 256 MiB,
+// the same at 16 MiB and 1 GiB; MAXP gained 7% at 64-256 MiB but lost 8% at
+// 1 GiB, so it keeps sixteen.
 static uint64_t pick_seg(cdc_handle h, cdc_alg alg, cdc_params p, uint64_t len, uint64_t n_files) {
     if (h->seg) return (uint64_t)h->seg;
     const uint64_t cap = alg == CDC_MAXP ? (512u << 10) : p.max >= (128u << 10) ? (256u << 10) : (384u << 10);
     const uint64_t floor = alg == CDC_MAXP ? (64u << 10) : (32u << 10);
-    uint64_t per = len / ((uint64_t)(h->sm_count > 0 ? h->sm_count : 148) * 16 + n_files);
+    const uint64_t per_sm = alg == CDC_MAXP ? 16 : 4;
+    uint64_t per = len / ((uint64_t)(h->sm_count > 0 ? h->sm_count : 148) * per_sm + n_files);
     uint64_t s = per < floor ? floor : per;
     if (s > cap) s = cap;
     return (s + 63) & ~63ull;
