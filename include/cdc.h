@@ -161,10 +161,26 @@ typedef enum {
                                  per thread while more than this many are
                                  alive, then one per warp (all 32 lanes share
                                  each step); 1..128, 0 = automatic (96) */
-    CDC_OPT_STARTS = 8        /* distinct speculative starts per segment, spread
+    CDC_OPT_STARTS = 8,       /* distinct speculative starts per segment, spread
                                  over its first `span` bytes; 1..128, 0 =
                                  automatic (span / 128, within 16..128;
                                  16 for MAXP) */
+    CDC_OPT_PIPELINE = 9,     /* chain stage of cdc_chunk / cdc_chunk_async /
+                                 cdc_chunk_host: 0 = automatic (the candidate
+                                 graph for inputs up to 256 MiB where it
+                                 applies: RAM and AE-Max with w >= 64 and
+                                 min <= w + 1, MAXP with 63 <= w <= 16384;
+                                 else speculation),
+                                 1 = speculative segments always,
+                                 2 = the candidate graph wherever it applies
+                                 (AE-Min included) */
+    CDC_OPT_GRAPH_SEGMENT = 10, /* bytes per segment of the candidate graph
+                                 (a multiple of 4096; raised to max if below);
+                                 0 = automatic */
+    CDC_OPT_GRAPH_SLOTS = 11  /* candidate slots per graph segment (1..4096,
+                                 rounded up to a multiple of 16; candidates
+                                 beyond them are stepped, slower but exact);
+                                 0 = automatic (segment / 32) */
 } cdc_option;
 
 CDC_API cdc_status cdc_set_option(cdc_handle h, cdc_option opt, int64_t value);

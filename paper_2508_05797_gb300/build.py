@@ -20,8 +20,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "--expt-relaxed-constexpr", "-Xcompiler", "-pthread", "-I", CSRC, "-I", INCLUDE]
-SOURCES = ["api.cu", "summarize.cu", "chain.cu", "batch.cu", "serve.cu", "prims.cu", "feed.cu"]
-HEADERS = ["chain_logic.cuh", "cdc_device.cuh", "cdc_launch.h", "warp_rules.cuh", "warp_fast.cuh"]
+SOURCES = ["api.cu", "summarize.cu", "chain.cu", "graph.cu", "batch.cu", "serve.cu", "prims.cu", "feed.cu"]
+HEADERS = ["chain_logic.cuh", "graph_logic.cuh", "cdc_device.cuh", "cdc_launch.h", "warp_rules.cuh", "warp_fast.cuh"]
 
 
 def nvcc() -> str:

@@ -18,6 +18,10 @@ OPT_PROFILE = 5
 OPT_STATS = 6
 OPT_WARP_CHAINS = 7
 OPT_STARTS = 8
+OPT_PIPELINE = 9        # 0 automatic, 1 speculative segments, 2 candidate graph
+OPT_GRAPH_SEGMENT = 10
+OPT_GRAPH_SLOTS = 11
+PIPE_AUTO, PIPE_SPECULATE, PIPE_GRAPH = 0, 1, 2
 STAT_NAMES = ["segments", "thread_steps", "warp_steps", "merges", "stitch_walks", "stitch_steps", "unknown",
               "hash_full", "scan_follows", "out_steps", "empty", "survivors", "cyc_setup", "cyc_threads",
               "cyc_warps", "cyc_stitch", "rounds", "cyc_rounds", "cyc_surv", "stitch_long", "stitch_maxw",

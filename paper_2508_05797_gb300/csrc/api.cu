@@ -10,6 +10,7 @@
 #include "../../include/cdc.h"
 #include "cdc_device.cuh"
 #include "cdc_launch.h"
+#include "graph_logic.cuh"
 
 using namespace cdc;
 
@@ -43,9 +44,41 @@ struct cdc_handle_s {
     uint64_t* host_out = nullptr;
     size_t host_out_cap = 0;
     Ctrl* pinned_ctrl = nullptr;  // page-locked copy of the control block
+    // candidate-graph chain stage (graph.cu)
+    uint32_t* g_cpos = nullptr;
+    size_t g_cpos_cap = 0;
+    uint32_t* g_cft = nullptr;
+    size_t g_cft_cap = 0;
+    uint32_t* g_csc = nullptr;
+    size_t g_csc_cap = 0;
+    unsigned long long* g_cex = nullptr;
+    size_t g_cex_cap = 0;
+    uint32_t* g_cnum = nullptr;
+    size_t g_cnum_cap = 0;
+    uint32_t* g_sent = nullptr;
+    size_t g_sent_cap = 0;
+    uint64_t* g_soff = nullptr;
+    size_t g_soff_cap = 0;
+    unsigned long long* g_uex = nullptr;
+    size_t g_uex_cap = 0;
+    uint32_t* g_uent = nullptr;
+    size_t g_uent_cap = 0;
+    uint64_t* g_uoff = nullptr;
+    size_t g_uoff_cap = 0;
+    uint8_t* g_tmax = nullptr;
+    size_t g_tmax_cap = 0;
+    uint8_t* g_cval = nullptr;
+    size_t g_cval_cap = 0;
+    unsigned long long* g_ticket = nullptr;
+    size_t g_ticket_cap = 0;
+    uint8_t* g_cfar = nullptr;
+    size_t g_cfar_cap = 0;
+    uint32_t* g_far = nullptr;
+    size_t g_far_cap = 0;
     // options
     int64_t seg = 0, span = 0, timeout_ms = 2000, force_bytes = 0, hold_item = -1, stats = 0, warp_chains = 0;
     int64_t starts = 0;
+    int64_t pipeline = 0, graph_seg = 0, graph_cap = 0;
     // last-call bookkeeping
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // start, summaries done, end, speculation done
     bool timed = false;
@@ -138,6 +171,21 @@ extern "C" cdc_status cdc_destroy(cdc_handle h) {
     cudaFree(h->item_file);
     cudaFree(h->host_stage);
     cudaFree(h->host_out);
+    cudaFree(h->g_cpos);
+    cudaFree(h->g_cft);
+    cudaFree(h->g_csc);
+    cudaFree(h->g_cex);
+    cudaFree(h->g_cnum);
+    cudaFree(h->g_sent);
+    cudaFree(h->g_soff);
+    cudaFree(h->g_uex);
+    cudaFree(h->g_uent);
+    cudaFree(h->g_uoff);
+    cudaFree(h->g_tmax);
+    cudaFree(h->g_cval);
+    cudaFree(h->g_ticket);
+    cudaFree(h->g_cfar);
+    cudaFree(h->g_far);
     if (h->pinned_ctrl) cudaFreeHost(h->pinned_ctrl);
     for (int i = 0; i < 4; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
@@ -178,6 +226,18 @@ extern "C" cdc_status cdc_set_option(cdc_handle h, cdc_option opt, int64_t v) {
         if (v < 0 || v > NL) return CDC_ERR_INVALID;
         h->starts = v;
         return CDC_OK;
+    case CDC_OPT_PIPELINE:
+        if (v < 0 || v > 2) return CDC_ERR_INVALID;
+        h->pipeline = v;
+        return CDC_OK;
+    case CDC_OPT_GRAPH_SEGMENT:
+        if (v < 0 || v > (1ll << 26) || (v & 4095)) return CDC_ERR_INVALID;
+        h->graph_seg = v;
+        return CDC_OK;
+    case CDC_OPT_GRAPH_SLOTS:
+        if (v < 0 || v > 4096) return CDC_ERR_INVALID;
+        h->graph_cap = v;
+        return CDC_OK;
     case CDC_OPT_PROFILE:
         if (v && !h->prof_ev) {
             cudaSetDevice(h->device);
@@ -206,6 +266,9 @@ extern "C" cdc_status cdc_get_option(cdc_handle h, cdc_option opt, int64_t* v) {
     case CDC_OPT_STATS: *v = h->stats; return CDC_OK;
     case CDC_OPT_WARP_CHAINS: *v = h->warp_chains; return CDC_OK;
     case CDC_OPT_STARTS: *v = h->starts; return CDC_OK;
+    case CDC_OPT_PIPELINE: *v = h->pipeline; return CDC_OK;
+    case CDC_OPT_GRAPH_SEGMENT: *v = h->graph_seg; return CDC_OK;
+    case CDC_OPT_GRAPH_SLOTS: *v = h->graph_cap; return CDC_OK;
     default: return CDC_ERR_INVALID;
     }
 }
@@ -340,6 +403,179 @@ static Geo geometry(const uint8_t* data, uint64_t len) {
     return g;
 }
 
+// ---- candidate-graph chain stage (graph.cu) ------------------------------------
+
+static constexpr uint64_t kGraphAutoMax = 256ull << 20;
+
+struct GraphGeo {
+    uint64_t S;
+    uint32_t nseg, cap, G, nunit, win;
+};
+
+// Does the call take the candidate graph, and with which geometry? The graph
+// needs every natural cut to be a candidate: min <= w + 1 for RAM and AE (the
+// cut never depends on min), w >= 64 so that the block rules apply, MAXP from
+// block targets. Segments of S >= max bytes (64 KiB, 128 KiB from 256 MiB on),
+// S / 32 candidate slots each; units of about sqrt(segments) segments.
+static bool use_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan& pl, uint64_t len, GraphGeo* gg) {
+    if (h->pipeline == 1 || h->force_bytes) return false;
+    // automatic: the graph for inputs up to kGraphAutoMax (measured faster there;
+    // beyond it the speculative segments are faster)
+    if (h->pipeline == 0 && len > kGraphAutoMax) return false;
+    switch (pl.rule) {
+    case RULE_RAM:
+    case RULE_AE:
+        if (p.w < 64 || (uint64_t)p.min > (uint64_t)p.w + 1) return false;
+        if (alg == CDC_AE_MIN && h->pipeline != 2) return false;
+        break;
+    case RULE_MAXP: break;
+    default: return false;
+    }
+    uint64_t S = h->graph_seg ? (uint64_t)h->graph_seg : (len >= (256ull << 20) ? (128u << 10) : (64u << 10));
+    const uint64_t mx4k = ((uint64_t)p.max + 4095) & ~4095ull;
+    if (S < mx4k) S = mx4k;
+    if (S > (64ull << 20)) return false;
+    uint64_t cap = h->graph_cap ? (uint64_t)h->graph_cap : S / 32;
+    cap = (cap + 15) & ~15ull;  // slots start 16-byte aligned for vector loads
+    if (cap > 4096) cap = 4096;
+    if (cap < 16) cap = 16;
+    const uint64_t nseg = (len + S - 1) / S;
+    if (nseg == 0 || nseg * cap >= (uint64_t)GID_NONE) return false;
+    gg->S = S;
+    gg->nseg = (uint32_t)nseg;
+    gg->cap = (uint32_t)cap;
+    if (nseg <= 32) {
+        gg->G = (uint32_t)nseg;
+    } else {
+        uint32_t G = 1;
+        while ((uint64_t)G * G < nseg) G++;
+        gg->G = G;
+    }
+    gg->nunit = (uint32_t)((nseg + gg->G - 1) / gg->G);
+    // summaries staged per segment by the local kernel: the segment, max past
+    // it and the windows around (multiple of 16 blocks)
+    uint64_t win = (2 * S + 2ull * p.w + 256 + 63) / 64 + 32;
+    win = (win + 15) & ~15ull;
+    if (win > (8u << 10)) win = 8u << 10;
+    gg->win = (uint32_t)win;
+    return true;
+}
+
+static cdc_status run_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan& pl, const Geo& g,
+                            const GraphGeo& gg, uint64_t* out, uint64_t capacity, uint64_t* d_count,
+                            cudaStream_t st) {
+    (void)alg;
+    cdc_status s;
+    const size_t slots = (size_t)gg.nseg * gg.cap;
+    if ((s = grow(&h->g_cpos, &h->g_cpos_cap, slots, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_cval, &h->g_cval_cap, slots, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_ticket, &h->g_ticket_cap, 2, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_cft, &h->g_cft_cap, slots, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_csc, &h->g_csc_cap, slots, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_cex, &h->g_cex_cap, slots, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_cnum, &h->g_cnum_cap, (size_t)gg.nseg, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_sent, &h->g_sent_cap, (size_t)gg.nseg, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_soff, &h->g_soff_cap, (size_t)gg.nseg, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_uex, &h->g_uex_cap, slots, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_cfar, &h->g_cfar_cap, slots, false, st)) != CDC_OK) return s;
+    const size_t far_cap = (size_t)gg.nseg * 64 + 1024;
+    if ((s = grow(&h->g_far, &h->g_far_cap, far_cap, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_uent, &h->g_uent_cap, (size_t)gg.nunit, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_uoff, &h->g_uoff_cap, (size_t)gg.nunit, false, st)) != CDC_OK) return s;
+    h->launches = 0;
+    const bool rec = !capturing(st);
+    h->timed = false;
+    cudaEvent_t* ev = h->ev;
+    if (rec && h->profile && h->prof_n < cdc_handle_s::PROF_CAP) ev = h->prof_ev + 4 * h->prof_n++;
+    if (h->stats) cudaMemsetAsync(h->ctrl->stats, 0, sizeof(h->ctrl->stats), st);
+    if (rec) cudaEventRecord(ev[0], st);
+    {
+        SumLaunch a;
+        a.base = g.base;
+        a.lo = g.lo; a.hi = g.hi; a.glo = g.glo; a.ghi = g.ghi;
+        a.nblk = g.nblk;
+        a.smax = h->smax;
+        a.sarg = h->sarg;
+        a.ssup = h->ssup;
+        a.nsup = g.nsup;
+        a.w = p.w;
+        a.halo_blocks = pl.halo;
+        a.timeout_ns = (uint64_t)h->timeout_ms * 1000000ull;
+        a.ctrl = h->ctrl;
+        uint64_t tiles = summary_tiles(pl.sum, g.nblk);
+        uint64_t grid = (uint64_t)h->sm_count * summary_blocks_per_sm(pl.sum, pl.halo);
+        if (grid > tiles) grid = tiles;
+        if (grid < 1) grid = 1;
+        if (launch_summary(a, pl.sum, (int)grid, st) != cudaSuccess) return CDC_ERR_CUDA;
+        h->launches++;
+    }
+    if (rec) cudaEventRecord(ev[1], st);
+    GraphLaunch ga;
+    memset(&ga, 0, sizeof ga);
+    ga.base = g.base;
+    ga.lo = g.lo;
+    ga.hi = g.hi;
+    ga.smax = h->smax;
+    ga.sarg = h->sarg ? h->sarg : h->smax;
+    ga.ssup = h->ssup;
+    ga.w = p.w; ga.mn = p.min; ga.mx = p.max;
+    ga.inv = pl.inv;
+    ga.S = gg.S;
+    ga.nseg = gg.nseg;
+    ga.cap = gg.cap;
+    ga.G = gg.G;
+    ga.nunit = gg.nunit;
+    ga.win = gg.win;
+    ga.cpos = h->g_cpos;
+    ga.cval = h->g_cval;
+    ga.ticket = h->g_ticket;
+    ga.cnum = h->g_cnum;
+    ga.cft = h->g_cft;
+    ga.csc = h->g_csc;
+    ga.cex = h->g_cex;
+    ga.cux = h->g_uex;
+    ga.cfar = h->g_cfar;
+    ga.far_list = h->g_far;
+    ga.far_cap = (uint32_t)far_cap;
+    ga.uent = h->g_uent;
+    ga.uoff = h->g_uoff;
+    ga.sent = h->g_sent;
+    ga.soff = h->g_soff;
+    ga.out = out;
+    ga.capacity = capacity;
+    ga.d_count = d_count;
+    ga.ctrl = h->ctrl;
+    ga.stats = h->stats ? h->ctrl->stats : nullptr;
+    // window-maximum table (written by the candidate kernel, read by F)
+    if (pl.rule != RULE_MAXP && p.w >= 128 && p.w / 64 <= 1000) {
+        uint64_t qa, qb;
+        const Prm P{p.w, p.min, p.max};
+        if (pl.rule == RULE_RAM) cand_source_range<RULE_RAM>(P, g.lo, g.hi, &qa, &qb);
+        else cand_source_range<RULE_AE>(P, g.lo, g.hi, &qa, &qb);
+        if (qa < qb) {
+            ga.tmax = h->g_tmax;
+            ga.tlev = tview_level(p.w);
+            ga.tb0 = qa >> 6;
+            ga.tb1 = ((qb - 1) >> 6) + 1;
+        }
+    }
+    const uint64_t sms = (uint64_t)(h->sm_count > 0 ? h->sm_count : 148);
+    auto clampg = [](uint64_t want, uint64_t lim) { return (int)(want < lim ? (want > 0 ? want : 1) : lim); };
+    GraphGrids gr;
+    gr.cand = clampg(gg.nseg, sms * 8);
+    gr.local = clampg(gg.nseg, sms * (uint64_t)graph_local_blocks_per_sm(pl.rule, gg.cap, gg.win));
+    gr.unit = clampg(gg.nunit, 65535);
+    gr.emit = clampg(gg.nseg, sms * 32);
+    if (launch_graph(ga, pl.rule, gr, st, &h->launches, rec ? ev[3] : nullptr) != cudaSuccess) return CDC_ERR_CUDA;
+    if (rec) {
+        cudaEventRecord(ev[2], st);
+        h->last_ev = ev;
+        h->timed = true;
+    }
+    h->prof_launches += h->launches;
+    return CDC_OK;
+}
+
 // launch the summary and chain stages; n_files == 0 means one stream
 static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* data, uint64_t len,
                       const uint64_t* d_file_off, uint64_t n_files, uint64_t* out, uint64_t capacity,
@@ -351,13 +587,19 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     const bool batch = d_file_off != nullptr;
     const uint64_t seg = pick_seg(h, alg, p, len, batch ? n_files : 1);
     const uint64_t items = batch ? len / seg + n_files + 1 : (len + seg - 1) / seg;
+    GraphGeo gg;
+    const bool graph = !batch && ctx == 0 && use_graph(h, alg, p, pl, len, &gg);
     cdc_status s;
     if (pl.sum != SUM_NONE) {
-        const size_t need = g.nblk_pad + 64;
+        // the graph's candidate kernel stages up to 1032 blocks past the data
+        const size_t need = g.nblk_pad + (graph ? 2112 : 64);
         if ((s = grow(&h->smax, &h->sum_cap, need, false, st)) != CDC_OK) return s;
         if (pl.sum != SUM_MAXP && (s = grow(&h->sarg, &h->sarg_cap, need, false, st)) != CDC_OK) return s;
         if ((s = grow(&h->ssup, &h->ssup_cap, g.nsup + 64, false, st)) != CDC_OK) return s;
+        if (graph && pl.rule != RULE_MAXP && (s = grow(&h->g_tmax, &h->g_tmax_cap, need, false, st)) != CDC_OK)
+            return s;
     }
+    if (graph) return run_graph(h, alg, p, pl, g, gg, out, capacity, d_count, st);
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, st)) != CDC_OK) return s;
     if ((s = grow(&h->hash, &h->hash_cap, items * seg_hash_bytes(), false, st)) != CDC_OK) return s;
     if ((s = grow(&h->plog, &h->plog_cap, items * seg_log_bytes(kLogCap), false, st)) != CDC_OK) return s;

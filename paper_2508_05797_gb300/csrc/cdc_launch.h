@@ -115,6 +115,77 @@ size_t group_state_bytes();
 cudaError_t launch_chain(const ChainLaunch& a, int rule, const ChainGrids& g, cudaStream_t st, int* launches,
                          cudaEvent_t ev_spec = nullptr);
 
+// ---- the candidate-graph chain stage (graph.cu) -------------------------------
+//
+// One stream [lo, hi) cut into nseg segments of S bytes (S >= max). Candidate
+// ids are seg * cap + index of the candidate in its segment's slot. Special ids:
+constexpr uint32_t GID_END = 0xFFFFFFFFu;   // the end of the data
+constexpr uint32_t GID_SLOW = 0xFFFFFFFEu;  // a candidate beyond its segment's slot
+constexpr uint32_t GID_NONE = 0xFFFFFFFDu;  // no entry
+
+struct GraphLaunch {
+    const uint8_t* base;
+    uint64_t lo, hi;         // physical positions of the data (offsets from base)
+    const uint8_t* smax;
+    const uint8_t* sarg;
+    const uint8_t* ssup;
+    uint32_t w, mn, mx;
+    uint32_t inv;
+    uint64_t S;              // segment bytes (multiple of 64, >= mx)
+    uint32_t nseg;
+    uint32_t cap;            // candidate slots per segment
+    uint32_t G;              // segments per unit of the unit tables
+    uint32_t nunit;          // ceil(nseg / G); 1 = no unit tables
+    uint32_t win;            // block maxima staged per segment by the local kernel
+    // window-maximum table written by k_gcand (RAM / AE with 128 <= w < 64 KiB):
+    // tmax[b] = max of the block maxima [b, b + 2^tlev), valid for b in [tb0, tb1)
+    uint8_t* tmax;           // null: no table
+    uint32_t tlev;
+    uint64_t tb0, tb1;
+    uint32_t* cpos;          // [nseg * cap] candidate position - segment start
+    uint8_t* cval;           // [nseg * cap] its source byte (RAM: the cut byte; AE: the target)
+    uint32_t* cnum;          // [nseg] candidates of the segment (may exceed cap)
+    uint32_t* cft;           // [nseg * cap] id of F(candidate)
+    uint32_t* csc;           // [nseg * cap] chunk ends from the candidate to F(candidate)
+    unsigned long long* cex; // [nseg * cap] (ends << 32) | id of the first candidate past the segment
+    unsigned long long* cux; // [nseg * cap] the same past the unit: for the unit's first segment and far landings
+    uint8_t* cfar;           // [nseg * cap] 1: cux holds the candidate's unit exit (a far landing)
+    uint32_t* far_list;      // far landings (F targets past the next segment), in no order
+    uint32_t far_cap;
+    uint32_t* uent;          // [nunit] id of the true chain's first candidate in the unit, or GID_NONE
+    uint64_t* uoff;          // [nunit] boundaries before it
+    uint32_t* sent;          // [nseg] id of the true chain's entry in the segment, or GID_NONE
+    uint64_t* soff;          // [nseg] boundaries before it
+    uint64_t* out;
+    uint64_t capacity;
+    uint64_t* d_count;
+    Ctrl* ctrl;
+    unsigned long long* ticket;  // [2]: work counter of the local kernel, far landings listed (zeroed by k_gcand)
+    unsigned long long* stats;   // counters GST_* (testing only), or null
+};
+// counters of the candidate graph (Ctrl::stats when CDC_OPT_STATS is on)
+enum : int {
+    GST_SEGMENTS = 0,      // segments the local kernel processed
+    GST_CANDS = 1,         // candidates
+    GST_GENERIC = 2,       // F by stepping the chain (the list could not decide)
+    GST_CYC_STAGE = 3,     // local kernel cycles, summed over segments: staging lists, maxima, table
+    GST_CYC_F = 4,         //   F of the segment's candidates
+    GST_CYC_JUMP = 5,      //   pointer jumping
+    GST_ROUNDS = 6,        // jumping rounds, summed
+    GST_MAX_SEG = 7,       // the longest segment (cycles)
+    GST_CYC_GENERIC = 8,   // cycles of the stepped F, summed over candidates
+    GST_MAX_GENERIC = 9    // the longest stepped F (cycles)
+};
+
+struct GraphGrids {
+    int cand, local, unit, emit;
+};
+// dynamic shared memory of the local kernel (cap slots, win staged summary blocks)
+int graph_local_smem(int rule, uint32_t cap, uint32_t win);
+int graph_local_blocks_per_sm(int rule, uint32_t cap, uint32_t win);
+cudaError_t launch_graph(const GraphLaunch& a, int rule, const GraphGrids& g, cudaStream_t st, int* launches,
+                         cudaEvent_t ev_mid = nullptr);
+
 // batch set-up: item_off (n_files + 1), item_file, ctrl->n_items
 cudaError_t launch_batch_setup(const uint64_t* file_off, uint64_t n_files, uint64_t seg, uint64_t* item_off,
                                uint32_t* item_file, uint64_t* scan_tmp, Ctrl* ctrl, cudaStream_t st,

@@ -21,7 +21,7 @@ def load():
         if _lib is not None:
             return _lib
         os.makedirs(os.path.dirname(OUT), exist_ok=True)
-        deps = [SRC, os.path.join(CSRC, "chain_logic.cuh")]
+        deps = [SRC, os.path.join(CSRC, "chain_logic.cuh"), os.path.join(CSRC, "graph_logic.cuh")]
         if not os.path.exists(OUT) or any(os.path.getmtime(d) > os.path.getmtime(OUT) for d in deps):
             tmp = OUT + ".%d.tmp" % os.getpid()
             subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC, SRC, "-o", tmp])
@@ -36,5 +36,20 @@ def load():
         lib.hc_chain_adv.restype = u64
         lib.hc_block_max_first.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
         lib.hc_block_max_first.restype = None
+        gargs = [i32, vp, vp, vp, vp, u32, u32, u32, u32, u64, u64]
+        lib.hc_cands.argtypes = gargs + [vp, u64]
+        lib.hc_cands.restype = u64
+        lib.hc_is_cand.argtypes = gargs + [u64]
+        lib.hc_is_cand.restype = i32
+        lib.hc_cand_next.argtypes = gargs + [u64, ctypes.POINTER(u32)]
+        lib.hc_cand_next.restype = u64
+        lib.hc_graph_chain.argtypes = gargs + [vp, u64]
+        lib.hc_graph_chain.restype = u64
+        lib.hc_graph_chain_t.argtypes = gargs + [vp, u32, u64, u64, vp, u64]
+        lib.hc_graph_chain_t.restype = u64
+        lib.hc_list_check.argtypes = gargs + [vp, vp, u32, u64, vp]
+        lib.hc_list_check.restype = u64
+        lib.hc_tview_level.argtypes = [u32]
+        lib.hc_tview_level.restype = u32
         _lib = lib
         return lib

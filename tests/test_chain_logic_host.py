@@ -149,7 +149,7 @@ def test_block_max_first_matches_numpy():
 
 def _superblocks(ar, alg):
     nsup = (ar.hi + 4095) // 4096 + 2
-    sup = np.zeros(nsup, dtype=np.uint8)
+    sup = np.zeros(nsup + 32, dtype=np.uint8)  # room for 16-byte reads past the end
     nblk = (ar.hi + 63) // 64
     if alg == "maxp":
         has = (ar.smax[:nblk] != 0xFF).astype(np.int64)

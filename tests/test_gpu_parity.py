@@ -107,9 +107,10 @@ def test_pathological_content(ck, kind):
 def test_tiny_segments_stress_lookback(ck, seg):
     """Many segments per chunk (and the reverse): stitching, look-back and
     the walks that settle entries the tables do not cover."""
-    from paper_2508_05797_gb300.cdc import OPT_SEGMENT, OPT_SPAN
+    from paper_2508_05797_gb300.cdc import OPT_PIPELINE, OPT_SEGMENT, OPT_SPAN, PIPE_SPECULATE
     data = synth.mixed_range(9, 64 * MIB, 3 * MIB, 2 * MIB + 333)
     try:
+        ck.set_option(OPT_PIPELINE, PIPE_SPECULATE)
         for span in (0, 64, 10_000):
             ck.set_option(OPT_SEGMENT, seg)
             ck.set_option(OPT_SPAN, span)
@@ -119,6 +120,7 @@ def test_tiny_segments_stress_lookback(ck, seg):
     finally:
         ck.set_option(OPT_SEGMENT, 0)
         ck.set_option(OPT_SPAN, 0)
+        ck.set_option(OPT_PIPELINE, 0)
 
 
 @pytest.mark.parametrize("starts", [1, 3, 16, 128])
@@ -126,9 +128,10 @@ def test_speculative_start_counts(ck, starts):
     """Any number of distinct speculative starts per segment gives the
     oracle's boundaries (few starts leave most entries to the stitch and the
     resolution walks)."""
-    from paper_2508_05797_gb300.cdc import OPT_SEGMENT, OPT_STARTS
+    from paper_2508_05797_gb300.cdc import OPT_PIPELINE, OPT_SEGMENT, OPT_STARTS, PIPE_SPECULATE
     data = synth.mixed_range(9, 64 * MIB, 5 * MIB, 2 * MIB + 77)
     try:
+        ck.set_option(OPT_PIPELINE, PIPE_SPECULATE)
         ck.set_option(OPT_STARTS, starts)
         for seg in (0, 4096):
             ck.set_option(OPT_SEGMENT, seg)
@@ -137,6 +140,7 @@ def test_speculative_start_counts(ck, starts):
     finally:
         ck.set_option(OPT_STARTS, 0)
         ck.set_option(OPT_SEGMENT, 0)
+        ck.set_option(OPT_PIPELINE, 0)
 
 
 def test_byte_rules_equal_summary_rules(ck):
@@ -198,11 +202,12 @@ def test_timeout_is_reported_and_handle_recovers(ck):
     """A segment that never publishes (test switch) makes its successors'
     bounded waits run out; the call returns CDC_ERR_TIMEOUT instead of
     hanging, and the next call on the same handle is correct."""
-    from paper_2508_05797_gb300.cdc import (ERR_TIMEOUT, OPT_DEBUG_HOLD_ITEM, OPT_SEGMENT, OPT_TIMEOUT_MS,
-                                            CdcError)
+    from paper_2508_05797_gb300.cdc import (ERR_TIMEOUT, OPT_DEBUG_HOLD_ITEM, OPT_PIPELINE, OPT_SEGMENT,
+                                            OPT_TIMEOUT_MS, PIPE_SPECULATE, CdcError)
     data = synth.uniform(5, 1 * MIB)
     t = to_device(data)
     try:
+        ck.set_option(OPT_PIPELINE, PIPE_SPECULATE)  # the speculative pipeline has the bounded waits
         ck.set_option(OPT_SEGMENT, 4096)
         ck.set_option(OPT_TIMEOUT_MS, 200)
         ck.set_option(OPT_DEBUG_HOLD_ITEM, 3)
@@ -213,6 +218,7 @@ def test_timeout_is_reported_and_handle_recovers(ck):
         ck.set_option(OPT_DEBUG_HOLD_ITEM, -1)
         ck.set_option(OPT_TIMEOUT_MS, 2000)
         ck.set_option(OPT_SEGMENT, 0)
+        ck.set_option(OPT_PIPELINE, 0)
     exp = oracle.chunk("ram", data, 700, 128, 8192)
     assert np.array_equal(ck.chunk(t, "ram", 700, 128, 8192).cpu().numpy().astype(np.uint64), exp)
 
