@@ -65,8 +65,10 @@ struct cdc_handle_s {
     size_t g_uent_cap = 0;
     uint64_t* g_uoff = nullptr;
     size_t g_uoff_cap = 0;
-    uint8_t* g_tmax = nullptr;
-    size_t g_tmax_cap = 0;
+    uint8_t* g_spre = nullptr;
+    size_t g_spre_cap = 0;
+    uint8_t* g_ssuf = nullptr;
+    size_t g_ssuf_cap = 0;
     uint8_t* g_cval = nullptr;
     size_t g_cval_cap = 0;
     unsigned long long* g_ticket = nullptr;
@@ -181,7 +183,8 @@ extern "C" cdc_status cdc_destroy(cdc_handle h) {
     cudaFree(h->g_uex);
     cudaFree(h->g_uent);
     cudaFree(h->g_uoff);
-    cudaFree(h->g_tmax);
+    cudaFree(h->g_spre);
+    cudaFree(h->g_ssuf);
     cudaFree(h->g_cval);
     cudaFree(h->g_ticket);
     cudaFree(h->g_cfar);
@@ -405,7 +408,8 @@ static Geo geometry(const uint8_t* data, uint64_t len) {
 
 // ---- candidate-graph chain stage (graph.cu) ------------------------------------
 
-static constexpr uint64_t kGraphAutoMax = 256ull << 20;
+static constexpr uint64_t kGraphAutoMax = 384ull << 20;
+static constexpr uint64_t kGraphAutoMaxAE = 768ull << 20;
 
 struct GraphGeo {
     uint64_t S;
@@ -415,13 +419,16 @@ struct GraphGeo {
 // Does the call take the candidate graph, and with which geometry? The graph
 // needs every natural cut to be a candidate: min <= w + 1 for RAM and AE (the
 // cut never depends on min), w >= 64 so that the block rules apply, MAXP from
-// block targets. Segments of S >= max bytes (64 KiB, 128 KiB from 256 MiB on),
-// S / 32 candidate slots each; units of about sqrt(segments) segments.
+// block targets. Segments of S >= max bytes (64 KiB below 256 MiB, 128 KiB
+// from there: on 16 MiB of the mixed stream 128 KiB was 1.3x slower for AE, on
+// uniform bytes 3% faster), S / 32 candidate slots each (a multiple of 16);
+// units of about sqrt(segments) segments.
 static bool use_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan& pl, uint64_t len, GraphGeo* gg) {
     if (h->pipeline == 1 || h->force_bytes) return false;
-    // automatic: the graph for inputs up to kGraphAutoMax (measured faster there;
-    // beyond it the speculative segments are faster)
-    if (h->pipeline == 0 && len > kGraphAutoMax) return false;
+    // automatic: the graph for inputs up to kGraphAutoMax (kGraphAutoMaxAE for
+    // AE), where it measured faster on the mixed stream at 4, 8 and 16 KiB
+    // means; beyond that the speculative segments are faster
+    if (h->pipeline == 0 && len > (pl.rule == RULE_AE ? kGraphAutoMaxAE : kGraphAutoMax)) return false;
     switch (pl.rule) {
     case RULE_RAM:
     case RULE_AE:
@@ -491,6 +498,7 @@ static cdc_status run_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan&
     if (rec) cudaEventRecord(ev[0], st);
     {
         SumLaunch a;
+        memset(&a, 0, sizeof a);
         a.base = g.base;
         a.lo = g.lo; a.hi = g.hi; a.glo = g.glo; a.ghi = g.ghi;
         a.nblk = g.nblk;
@@ -502,6 +510,10 @@ static cdc_status run_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan&
         a.halo_blocks = pl.halo;
         a.timeout_ns = (uint64_t)h->timeout_ms * 1000000ull;
         a.ctrl = h->ctrl;
+        if (pl.rule != RULE_MAXP) {
+            a.spre = h->g_spre;
+            a.ssuf = h->g_ssuf;
+        }
         uint64_t tiles = summary_tiles(pl.sum, g.nblk);
         uint64_t grid = (uint64_t)h->sm_count * summary_blocks_per_sm(pl.sum, pl.halo);
         if (grid > tiles) grid = tiles;
@@ -546,18 +558,10 @@ static cdc_status run_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan&
     ga.d_count = d_count;
     ga.ctrl = h->ctrl;
     ga.stats = h->stats ? h->ctrl->stats : nullptr;
-    // window-maximum table (written by the candidate kernel, read by F)
-    if (pl.rule != RULE_MAXP && p.w >= 128 && p.w / 64 <= 1000) {
-        uint64_t qa, qb;
-        const Prm P{p.w, p.min, p.max};
-        if (pl.rule == RULE_RAM) cand_source_range<RULE_RAM>(P, g.lo, g.hi, &qa, &qb);
-        else cand_source_range<RULE_AE>(P, g.lo, g.hi, &qa, &qb);
-        if (qa < qb) {
-            ga.tmax = h->g_tmax;
-            ga.tlev = tview_level(p.w);
-            ga.tb0 = qa >> 6;
-            ga.tb1 = ((qb - 1) >> 6) + 1;
-        }
+    // running maxima inside superblocks (written by the summary kernel)
+    if (pl.rule != RULE_MAXP) {
+        ga.spre = h->g_spre;
+        ga.ssuf = h->g_ssuf;
     }
     const uint64_t sms = (uint64_t)(h->sm_count > 0 ? h->sm_count : 148);
     auto clampg = [](uint64_t want, uint64_t lim) { return (int)(want < lim ? (want > 0 ? want : 1) : lim); };
@@ -596,8 +600,10 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
         if ((s = grow(&h->smax, &h->sum_cap, need, false, st)) != CDC_OK) return s;
         if (pl.sum != SUM_MAXP && (s = grow(&h->sarg, &h->sarg_cap, need, false, st)) != CDC_OK) return s;
         if ((s = grow(&h->ssup, &h->ssup_cap, g.nsup + 64, false, st)) != CDC_OK) return s;
-        if (graph && pl.rule != RULE_MAXP && (s = grow(&h->g_tmax, &h->g_tmax_cap, need, false, st)) != CDC_OK)
-            return s;
+        if (graph && pl.rule != RULE_MAXP) {
+            if ((s = grow(&h->g_spre, &h->g_spre_cap, need, false, st)) != CDC_OK) return s;
+            if ((s = grow(&h->g_ssuf, &h->g_ssuf_cap, need, false, st)) != CDC_OK) return s;
+        }
     }
     if (graph) return run_graph(h, alg, p, pl, g, gg, out, capacity, d_count, st);
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, st)) != CDC_OK) return s;
@@ -625,6 +631,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     if (rec) cudaEventRecord(ev[0], st);
     if (pl.sum != SUM_NONE) {
         SumLaunch a;
+        memset(&a, 0, sizeof a);
         a.base = g.base;
         a.lo = g.lo; a.hi = g.hi; a.glo = g.glo; a.ghi = g.ghi;
         a.nblk = g.nblk;
@@ -1097,6 +1104,7 @@ extern "C" cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t*
     int launches = 0;
     if (pl.sum != SUM_NONE) {
         SumLaunch a;
+        memset(&a, 0, sizeof a);
         a.base = g.base;
         a.lo = g.lo; a.hi = g.hi; a.glo = g.glo; a.ghi = g.ghi;
         a.nblk = g.nblk;

@@ -19,6 +19,8 @@ struct SumLaunch {
     uint8_t* smax;          // per block: max (RAM/AE) or target offset / 0xFF (MAXP)
     uint8_t* sarg;          // per block: first position of the max (RAM/AE)
     uint8_t* ssup;          // per 4 KiB superblock: max byte (RAM/AE) or target count (MAXP)
+    uint8_t* spre;          // RAM/AE, may be null: per block, the maximum of its superblock's blocks up to it
+    uint8_t* ssuf;          //   and from it to the superblock's end
     uint64_t nsup;          // superblocks covering [0, hi)
     uint32_t w;             // MAXP window
     uint32_t halo_blocks;   // MAXP: blocks staged on each side of a tile
@@ -137,11 +139,9 @@ struct GraphLaunch {
     uint32_t G;              // segments per unit of the unit tables
     uint32_t nunit;          // ceil(nseg / G); 1 = no unit tables
     uint32_t win;            // block maxima staged per segment by the local kernel
-    // window-maximum table written by k_gcand (RAM / AE with 128 <= w < 64 KiB):
-    // tmax[b] = max of the block maxima [b, b + 2^tlev), valid for b in [tb0, tb1)
-    uint8_t* tmax;           // null: no table
-    uint32_t tlev;
-    uint64_t tb0, tb1;
+    // RAM / AE: running maxima inside superblocks (the summary kernel's spre, ssuf)
+    const uint8_t* spre;     // null: none (MAXP)
+    const uint8_t* ssuf;
     uint32_t* cpos;          // [nseg * cap] candidate position - segment start
     uint8_t* cval;           // [nseg * cap] its source byte (RAM: the cut byte; AE: the target)
     uint32_t* cnum;          // [nseg] candidates of the segment (may exceed cap)
@@ -174,7 +174,12 @@ enum : int {
     GST_ROUNDS = 6,        // jumping rounds, summed
     GST_MAX_SEG = 7,       // the longest segment (cycles)
     GST_CYC_GENERIC = 8,   // cycles of the stepped F, summed over candidates
-    GST_MAX_GENERIC = 9    // the longest stepped F (cycles)
+    GST_MAX_GENERIC = 9,   // the longest stepped F (cycles)
+    GST_CC_STAGE = 10,     // candidate kernel cycles, summed over chunks: staging
+    GST_CC_LIST = 11,      //   listing the blocks that can hold a candidate
+    GST_CC_BLOCKS = 12,    //   testing the listed blocks' bytes
+    GST_CC_WRITE = 13,     //   writing the candidates
+    GST_CC_LISTED = 14     // blocks listed
 };
 
 struct GraphGrids {

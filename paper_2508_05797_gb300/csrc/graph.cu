@@ -92,7 +92,7 @@ __device__ unsigned long long g_slow_hop(const GraphLaunch& A, uint32_t id) {
     const Prm P{A.w, A.mn, A.mx};
     const RawView R{A.base, A.inv};
     const SumView S{A.smax, A.sarg, nullptr, nullptr, 0, 0, A.ssup};
-    const TView T{A.tmax, A.tmax ? A.tlev : 0xFFFFFFFFu, A.tb0, A.tb1};
+    const PreSuf T{A.spre, A.ssuf};
     const uint32_t k = id / A.cap;
     uint64_t y = g_pos(A, id);
     unsigned long long acc = 0;
@@ -123,8 +123,8 @@ __device__ __forceinline__ unsigned long long g_hop(const GraphLaunch& A, uint32
 // A candidate's byte is at least the maximum of the whole blocks its window
 // covers, and every source byte of a block shares those blocks but for two
 // partial ones; so per block the maximum L of the whole blocks common to all
-// its bytes' windows (a window of constant length, read from a sparse table of
-// block maxima in shared memory) rejects most blocks without reading them. The
+// its bytes' windows (two or three reads of the running maxima inside
+// superblocks) rejects most blocks without reading them. The
 // blocks that pass are listed, then read one per thread: bytes >= max(L, 1) are
 // flagged with packed compares; a flagged byte is a candidate if no flagged byte
 // before it (RAM) or after it (AE) in the block is greater and the partial
@@ -132,12 +132,15 @@ __device__ __forceinline__ unsigned long long g_hop(const GraphLaunch& A, uint32
 // first, raw bytes only where a block maximum is greater).
 
 constexpr uint32_t GC_CH = 2048;                 // source blocks per chunk
-constexpr uint32_t GC_KMAX = 1024;               // longest whole-block window kept in the table
-constexpr uint32_t GC_ST = GC_CH + 2 * GC_KMAX + 48;  // staged block maxima per chunk
+constexpr uint32_t GC_KMAX = 1024;               // longest whole-block window whose far end is staged
+constexpr uint32_t GC_ST = GC_CH + GC_KMAX + 256;  // staged blocks per chunk: the chunk, a halo on one side, 64-block alignment
 
 struct GcShared {
     __align__(16) uint8_t a[GC_ST];  // block maxima of [st0, st1)
-    uint8_t t[2][GC_ST];   // sparse-table levels
+    __align__(16) uint8_t pre[GC_ST];  // their running maxima inside superblocks
+    __align__(16) uint8_t suf[GC_ST];
+    __align__(16) uint8_t sup[GC_ST / 64 + 32];  // superblock maxima of [st0 / 64, ...)
+    uint8_t cv[GC_CH];     // listed block: the byte of its candidates if they share one, else 0
     uint16_t list[GC_CH];  // passing blocks (offsets from the chunk start)
     uint8_t lval[GC_CH];   // their L
     unsigned long long mask[GC_CH];
@@ -183,6 +186,23 @@ __device__ __forceinline__ bool gc_exceeds(const GraphLaunch& A, const RawView& 
     return false;
 }
 
+// maximum of the whole blocks [fb, lb) from the staged running maxima (the
+// blocks lie in [st0, st1), st0 a multiple of 64)
+__device__ __forceinline__ uint32_t gc_whole(const GcShared& sh, uint64_t st0, uint64_t fb, uint64_t lb) {
+    const uint64_t q0 = fb >> 6, q1 = (lb - 1) >> 6;
+    uint32_t M;
+    if (q0 == q1) {
+        if ((fb & 63) == 0) return sh.pre[lb - 1 - st0];
+        if ((lb & 63) == 0) return sh.suf[fb - st0];
+        M = 0;
+        for (uint64_t x = fb; x < lb; x++) M = max(M, (uint32_t)sh.a[x - st0]);
+        return M;
+    }
+    M = max((uint32_t)sh.suf[fb - st0], (uint32_t)sh.pre[lb - 1 - st0]);
+    for (uint64_t q = q0 + 1; q < q1; q++) M = max(M, (uint32_t)sh.sup[q - (st0 >> 6)]);
+    return M;
+}
+
 template <int RULE>
 __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
     __shared__ GcShared sh;
@@ -199,16 +219,12 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
     uint32_t K = 0;
     if (RULE == RULE_RAM) K = w >= 126 ? (uint32_t)((w - 126 + 63) >> 6) : 0;
     if (RULE == RULE_AE) K = (uint32_t)((w + 1) >> 6) - 1;
-    // the sparse table's level: 2^lev <= floor(w / 64) - 1 (tview_level); K is
-    // that or one more, so two entries of the level cover K blocks
-    const uint32_t lev = tview_level(A.w) == 0xFFFFFFFFu ? 0u : tview_level(A.w);
-    const bool table = K > 0 && K <= GC_KMAX && tview_level(A.w) != 0xFFFFFFFFu;
-    const uint32_t span = 1u << lev;
-    // staged around a chunk: its blocks, and with the table the window's whole
-    // blocks and the partial ones at its far end, and the blocks the table
-    // entries of the chunk's last blocks reach (at most GC_ST in all)
+    // blocks staged around a chunk: its blocks and, for windows of up to GC_KMAX
+    // whole blocks, the partial blocks at the far end of its bytes' windows
+    const bool table = K > 0 && K <= GC_KMAX;
     const uint32_t pre = (table && RULE == RULE_RAM) ? K + 2 : 0;
-    const uint32_t post = table ? (RULE == RULE_AE ? K + 3 : span) : 0;
+    const uint32_t post = (table && RULE == RULE_AE) ? K + 3 : 0;
+    const PreSuf V{A.spre, A.ssuf};
     for (uint32_t seg = blockIdx.x; seg < A.nseg; seg += gridDim.x) {
         const uint64_t a = g_seg_lo(A, seg), b = g_seg_hi(A, seg);
         uint32_t* slot = A.cpos + (uint64_t)seg * A.cap;
@@ -234,35 +250,24 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
         for (uint64_t cb0 = qa >> 6; qa < qb && cb0 <= bl; cb0 += GC_CH) {
             const uint64_t cb1 = umin64(cb0 + GC_CH, bl + 1);
             const uint32_t nb = (uint32_t)(cb1 - cb0);
+            long long c0 = A.stats ? clock64() : 0;
             uint64_t st0 = 0, st1 = 0;
             if (RULE != RULE_MAXP) {
-                st0 = (cb0 >= pre ? cb0 - pre : 0) & ~15ull;
-                st1 = (cb1 + post + 15) & ~15ull;
-                for (uint64_t q = tid; q < (st1 - st0) / 16; q += GC_THREADS)
+                st0 = (cb0 >= pre ? cb0 - pre : 0) & ~63ull;
+                st1 = (cb1 + post + 63) & ~63ull;
+                for (uint64_t q = tid; q < (st1 - st0) / 16; q += GC_THREADS) {
                     reinterpret_cast<uint4*>(sh.a)[q] = reinterpret_cast<const uint4*>(A.smax + st0)[q];
-                __syncthreads();
-                // sparse table: level j holds the maximum of 2^j blocks from each index
-                if (table && lev > 0) {
-                    const uint8_t* src = sh.a;
-                    const uint32_t n = (uint32_t)(st1 - st0);
-                    for (uint32_t j = 1; j <= lev; j++) {
-                        uint8_t* dst = sh.t[j & 1];
-                        const uint32_t h = 1u << (j - 1);
-                        for (uint32_t i = tid; i + h < n; i += GC_THREADS) {
-                            const uint8_t u = src[i], v = src[i + h];
-                            dst[i] = u > v ? u : v;
-                        }
-                        __syncthreads();
-                        src = dst;
+                    if (A.spre) {
+                        reinterpret_cast<uint4*>(sh.pre)[q] = reinterpret_cast<const uint4*>(A.spre + st0)[q];
+                        reinterpret_cast<uint4*>(sh.suf)[q] = reinterpret_cast<const uint4*>(A.ssuf + st0)[q];
                     }
                 }
-            }
-            const uint8_t* T = (RULE != RULE_MAXP && lev > 0) ? sh.t[lev & 1] : sh.a;
-            if (RULE != RULE_MAXP && table && A.tmax) {
-                for (uint32_t i = tid; i < nb; i += GC_THREADS) A.tmax[cb0 + i] = T[cb0 + i - st0];
+                for (uint64_t q = tid; q < (st1 - st0) / 64; q += GC_THREADS) sh.sup[q] = A.ssup[st0 / 64 + q];
+                __syncthreads();
             }
             if (tid == 0) sh.nlist = 0;
             __syncthreads();
+            long long c1 = A.stats ? clock64() : 0;
             // 1. list the blocks that can hold a candidate, in order
             for (uint32_t r0 = 0; r0 < nb; r0 += GC_THREADS) {
                 const uint32_t o = r0 + (uint32_t)tid;
@@ -276,12 +281,7 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
                         const uint32_t bm = sh.a[blk - st0];
                         if (K > 0) {
                             const uint64_t ws = RULE == RULE_RAM ? blk - K : blk + 1;  // window [ws, ws + K)
-                            if (table) {
-                                const uint32_t x = T[ws - st0], y = T[ws + K - (1u << lev) - st0];
-                                L = x > y ? x : y;
-                            } else {
-                                L = sum_max(S, ws, ws + K);
-                            }
+                            L = table && A.spre ? gc_whole(sh, st0, ws, ws + K) : whole_max(S, V, ws, ws + K);
                         }
                         pass = bm != 0 && bm >= L;
                     }
@@ -306,6 +306,7 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
                 __syncthreads();
             }
             const uint32_t nl = sh.nlist;
+            long long c2 = A.stats ? clock64() : 0;
             // 2. the candidates of each listed block
             for (uint32_t e = tid; e < nl; e += GC_THREADS) {
                 const uint64_t blk = cb0 + sh.list[e];
@@ -313,6 +314,7 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
                 const uint32_t oa = qa > b0 ? (uint32_t)(qa - b0) : 0u;
                 const uint32_t ob = qb < b0 + 64 ? (uint32_t)(qb - b0) : 64u;
                 unsigned long long m = 0;
+                uint32_t cv = 0, cv_mixed = 0;  // the candidates' common byte
                 if (RULE == RULE_MAXP) {
                     const uint32_t o = A.smax[blk];
                     if (o >= oa && o < ob) m = 1ull << o;
@@ -342,8 +344,11 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
                                 f &= f - 1;
                                 const uint32_t o = 4u * (uint32_t)i + k, x = (wd[i] >> (8 * k)) & 0xFFu;
                                 if (o >= oa && o < ob && x >= run_max &&
-                                    (x == 255u || !gc_exceeds(A, R, sh.a, st0, st1, b0 + o - w, h1, x)))
+                                    (x == 255u || !gc_exceeds(A, R, sh.a, st0, st1, b0 + o - w, h1, x))) {
                                     m |= 1ull << o;
+                                    cv_mixed |= cv != 0 && cv != x;
+                                    cv = x;
+                                }
                                 if (x > run_max) run_max = x;
                             }
                         }
@@ -358,16 +363,21 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
                                 const uint32_t k = bit >> 3;
                                 const uint32_t o = 4u * (uint32_t)i + k, x = (wd[i] >> (8 * k)) & 0xFFu;
                                 if (o >= oa && o < ob && x >= run_max &&
-                                    (x == 255u || !gc_exceeds(A, R, sh.a, st0, st1, t0, b0 + o + w + 1, x)))
+                                    (x == 255u || !gc_exceeds(A, R, sh.a, st0, st1, t0, b0 + o + w + 1, x))) {
                                     m |= 1ull << o;
+                                    cv_mixed |= cv != 0 && cv != x;
+                                    cv = x;
+                                }
                                 if (x > run_max) run_max = x;
                             }
                         }
                     }
                 }
                 sh.mask[e] = m;
+                sh.cv[e] = cv_mixed ? 0 : (uint8_t)cv;
             }
             __syncthreads();
+            long long c3 = A.stats ? clock64() : 0;
             // 3. positions, in block order
             const uint32_t per = (nl + GC_THREADS - 1) / GC_THREADS;
             const uint32_t e0 = (uint32_t)tid * per, e1 = e0 + per < nl ? e0 + per : nl;
@@ -378,12 +388,14 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
             for (uint32_t e = e0; e < e1; e++) {
                 unsigned long long m = sh.mask[e];
                 const uint64_t b0 = (cb0 + sh.list[e]) << 6;
+                const uint32_t cve = sh.cv[e];
                 while (m) {
                     const int o = __ffsll((long long)m) - 1;
                     m &= m - 1;
                     if (at < A.cap) {
                         slot[at] = (uint32_t)((b0 + (uint64_t)o + shf) - a);
-                        A.cval[(uint64_t)seg * A.cap + at] = RULE == RULE_MAXP ? 0 : (uint8_t)R.byte(b0 + (uint64_t)o);
+                        A.cval[(uint64_t)seg * A.cap + at] =
+                            RULE == RULE_MAXP ? 0 : (uint8_t)(cve ? cve : R.byte(b0 + (uint64_t)o));
                         A.cfar[(uint64_t)seg * A.cap + at] = 0;
                     }
                     at++;
@@ -391,6 +403,14 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
             }
             run += tot;
             __syncthreads();  // shared arrays are reused by the next chunk
+            if (A.stats && tid == 0) {
+                const long long c4 = clock64();
+                atomicAdd(&A.stats[GST_CC_STAGE], (unsigned long long)(c1 - c0));
+                atomicAdd(&A.stats[GST_CC_LIST], (unsigned long long)(c2 - c1));
+                atomicAdd(&A.stats[GST_CC_BLOCKS], (unsigned long long)(c3 - c2));
+                atomicAdd(&A.stats[GST_CC_WRITE], (unsigned long long)(c4 - c3));
+                atomicAdd(&A.stats[GST_CC_LISTED], (unsigned long long)nl);
+            }
         }
         if (tid == 0) A.cnum[seg] = run;
     }
@@ -402,46 +422,52 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
 // segment whose chains cross a long quiet stretch holds one CTA, not a
 // static share of the grid). The segment's candidates and the next
 // segment's are listed in shared memory with their bytes, next to the block
-// maxima around them and their window table, so F of a candidate
+// maxima around them and their running maxima inside superblocks, so F of a candidate
 // is a binary search, one or two window maxima and a comparison
 // (list_next); only forced cuts, quiet runs and list overflows step the chain
 // (cand_next_t). Then pointer jumping in shared memory gives every candidate
 // the first candidate on its chain past the segment and the chunk ends up to it.
 
 // shared memory of k_glocal: lists of 2 cap entries (positions, bytes), three
-// jumping arrays of cap words, and the staged block maxima and window table
-// (`win` bytes each)
+// jumping arrays of cap words, and the staged block maxima with their running
+// maxima inside superblocks (`win` bytes each)
 __host__ __device__ inline uint32_t gl_stage_off(uint32_t cap) { return (22u * cap + 15u) & ~15u; }
 int graph_local_smem(int rule, uint32_t cap, uint32_t win) {
-    return (int)gl_stage_off(cap) + (rule == RULE_MAXP ? 0 : 2 * (int)win);
+    return (int)gl_stage_off(cap) + (rule == RULE_MAXP ? 0 : 3 * (int)win);
 }
 
 // window maximum over bytes [a, b): blocks [sb0, sb0 + sn) staged (sm) with
-// the maxima of 2^lev blocks from each (tb, valid while the 2^lev blocks are
-// staged); ranges outside the staged blocks go to the global summaries
+// their running maxima inside superblocks (spr, ssf); ranges outside the
+// staged blocks go to the global summaries
 struct WMaxStaged {
-    const uint8_t* sm;
-    const uint8_t* tb;  // the window table for the staged blocks, or null
+    const uint8_t* sm;   // block maxima of blocks [sb0, sb0 + sn)
+    const uint8_t* spr;  // their running maxima inside superblocks, or null
+    const uint8_t* ssf;
     uint64_t sb0, sn;
-    uint32_t lev;
-    uint64_t tb0, tb1;  // table entries written by the candidate kernel
     const SumView* S;
-    const TView* T;
+    const PreSuf* T;
     const RawView* R;
     __device__ uint32_t whole(uint64_t fb, uint64_t lb) const {  // blocks [fb, lb), staged
-        const uint64_t span = 1ull << lev;
+        if (spr) {
+            const uint64_t q0 = fb >> 6, q1 = (lb - 1) >> 6;
+            if (q0 == q1) {
+                if ((fb & 63) == 0) return spr[lb - 1 - sb0];
+                if ((lb & 63) == 0) return ssf[fb - sb0];
+            } else {
+                uint32_t M = ssf[fb - sb0];
+                const uint32_t t = spr[lb - 1 - sb0];
+                if (t > M) M = t;
+                for (uint64_t q = q0 + 1; q < q1 && M < 255; q++) {
+                    const uint32_t u = S->sup[q];
+                    if (u > M) M = u;
+                }
+                return M;
+            }
+        }
         uint32_t M = 0;
-        if (tb && lb - fb >= span && fb >= tb0 && lb - span < tb1) {
-            M = tb[lb - span - sb0];
-            for (uint64_t x = fb; x < lb - span; x += span) {
-                const uint32_t t = tb[x - sb0];
-                if (t > M) M = t;
-            }
-        } else {
-            for (uint64_t x = fb; x < lb; x++) {
-                const uint32_t t = sm[x - sb0];
-                if (t > M) M = t;
-            }
+        for (uint64_t x = fb; x < lb; x++) {
+            const uint32_t t = sm[x - sb0];
+            if (t > M) M = t;
         }
         return M;
     }
@@ -483,7 +509,7 @@ __device__ __forceinline__ void g_copy_u8(uint8_t* dst, const uint8_t* src, uint
 }
 
 template <int RULE>
-__global__ void __launch_bounds__(GL_THREADS) k_glocal(GraphLaunch A) {
+__global__ void __launch_bounds__(GL_THREADS, 1) k_glocal(GraphLaunch A) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t cap = A.cap;
     uint32_t* lpos = reinterpret_cast<uint32_t*>(smem);  // own then next segment's candidates - segment start
@@ -492,14 +518,14 @@ __global__ void __launch_bounds__(GL_THREADS) k_glocal(GraphLaunch A) {
     uint32_t* X = C + cap;                                // exit id (valid once J is GL_EXIT)
     uint8_t* lval = reinterpret_cast<uint8_t*>(X + cap);  // the candidates' bytes
     uint8_t* sm = smem + gl_stage_off(cap);               // staged block maxima
-    uint8_t* tb[1] = {sm + A.win};                        // the window table of the staged blocks
+    uint8_t* spr = sm + A.win;                            // running maxima inside superblocks (staged)
+    uint8_t* ssf = sm + 2 * A.win;
     __shared__ uint32_t s_seg;
     const int tid = threadIdx.x;
     const Prm P{A.w, A.mn, A.mx};
     const RawView R{A.base, A.inv};
     const SumView S{A.smax, A.sarg, nullptr, nullptr, 0, 0, A.ssup};
-    const TView T{A.tmax, A.tmax ? A.tlev : 0xFFFFFFFFu, A.tb0, A.tb1};
-    const uint32_t lev = A.tmax ? A.tlev : 0u;
+    const PreSuf T{A.spre, A.ssuf};
     const uint64_t nblk_all = ((A.hi + 63) >> 6) + 16;
     unsigned long long* st = A.stats;  // counters (testing only)
     for (;;) {
@@ -548,12 +574,15 @@ __global__ void __launch_bounds__(GL_THREADS) k_glocal(GraphLaunch A) {
             if (sb0 + sn > lim) sn = lim > sb0 ? lim - sb0 : 0;
             for (uint32_t q = tid; q < sn / 16; q += GL_THREADS) {
                 reinterpret_cast<uint4*>(sm)[q] = reinterpret_cast<const uint4*>(A.smax + sb0)[q];
-                if (A.tmax) reinterpret_cast<uint4*>(tb[0])[q] = reinterpret_cast<const uint4*>(A.tmax + sb0)[q];
+                if (A.spre) {
+                    reinterpret_cast<uint4*>(spr)[q] = reinterpret_cast<const uint4*>(A.spre + sb0)[q];
+                    reinterpret_cast<uint4*>(ssf)[q] = reinterpret_cast<const uint4*>(A.ssuf + sb0)[q];
+                }
             }
         }
         __syncthreads();
         long long t1 = st ? clock64() : 0;
-        const WMaxStaged wm{sm, A.tmax ? tb[0] : nullptr, sb0, sn, lev, A.tb0, A.tb1, &S, &T, &R};
+        const WMaxStaged wm{sm, A.spre ? spr : nullptr, ssf, sb0, sn, &S, &T, &R};
         const CandList L{lpos, lval, n + nla, a, cover};
         for (uint32_t i = tid; i < n; i += GL_THREADS) {
             const uint64_t y = a + lpos[i];
@@ -728,8 +757,11 @@ __global__ void k_gtop(GraphLaunch A) {
             const uint32_t k = id / A.cap, u = k / A.G;
             A.uent[u] = id;
             A.uoff[u] = off;
-            if (k == u * A.G || A.cfar[id]) {
-                next(A.cux[id]);
+            // both loads at once: the flag decides which one the hop uses
+            const unsigned long long vu = A.cux[id];
+            const uint8_t far = A.cfar[id];
+            if (k == u * A.G || far) {
+                next(vu);
             } else {
                 const uint32_t kend = (u + 1) * A.G;
                 while (id < GID_NONE && id / A.cap < kend) next(g_hop<RULE>(A, id));

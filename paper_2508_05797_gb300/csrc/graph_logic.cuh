@@ -361,43 +361,44 @@ CDC_HD uint64_t advance_far(const SumView& S, const RawView& R, const Prm& P, ui
     return e1;
 }
 
-// ---- window maxima from a table of 2^lev-block maxima -----------------------
+// ---- window maxima from running maxima inside superblocks ------------------
 //
-// t[b] = max m[b .. b + 2^lev) for blocks b in [b0, b1) (t == null: no table).
-// Any window of w >= 128 bytes holds between floor(w/64) - 1 and floor(w/64)
-// whole blocks; with 2^lev <= floor(w/64) - 1 two overlapping table entries
-// cover them, so a window maximum costs two table reads plus the partial end
-// blocks (raw bytes only where their block maximum could raise it).
-struct TView {
-    const uint8_t* t;
-    uint32_t lev;
-    uint64_t b0, b1;
+// pre[b] = max m[] over the blocks of b's 4 KiB superblock up to b, suf[b] =
+// from b to the superblock's end (written by the summary kernel), sup[q] = the
+// superblock's maximum. The maximum of whole blocks [fb, lb) spanning two or
+// more superblocks is max(suf[fb], sup of the superblocks between, pre[lb - 1]),
+// two or three reads for the windows of the configured workloads; a range
+// inside one superblock that touches either end is one read.
+struct PreSuf {
+    const uint8_t* pre;  // null: no running maxima
+    const uint8_t* suf;
 };
 
-CDC_HD uint32_t tview_level(uint32_t w) {
-    const uint32_t k = w >= 128 ? w / 64 - 1 : 0;
-    uint32_t lev = 0;
-    while (k > 0 && (2u << lev) <= k) lev++;
-    return k > 0 ? lev : 0xFFFFFFFFu;
-}
-
 // maximum of the whole blocks [fb, lb) (fb < lb)
-CDC_HD uint32_t whole_max(const SumView& S, const TView& T, uint64_t fb, uint64_t lb) {
-    const uint64_t span = 1ull << (T.lev & 31);
-    if (T.t && T.lev != 0xFFFFFFFFu && lb - fb >= span && lb - fb <= 2 * span && fb >= T.b0 &&
-        lb - span < T.b1) {
-        const uint32_t x = T.t[fb], y = T.t[lb - span];
-        return x > y ? x : y;
+CDC_HD uint32_t whole_max(const SumView& S, const PreSuf& V, uint64_t fb, uint64_t lb) {
+    if (!V.pre || !S.sup) return sum_max(S, fb, lb);
+    const uint64_t q0 = fb >> 6, q1 = (lb - 1) >> 6;
+    if (q0 == q1) {
+        if ((fb & 63) == 0) return V.pre[lb - 1];
+        if ((lb & 63) == 0) return V.suf[fb];
+        return sum_max(S, fb, lb);
     }
-    return sum_max(S, fb, lb);
+    uint32_t M = V.suf[fb];
+    const uint32_t t = V.pre[lb - 1];
+    if (t > M) M = t;
+    for (uint64_t q = q0 + 1; q < q1 && M < 255; q++) {
+        const uint32_t u = S.sup[q];
+        if (u > M) M = u;
+    }
+    return M;
 }
 
-// Extreme Byte Search over [a, b) with the table (equals range_max)
-CDC_HD uint32_t range_max_t(const SumView& S, const TView& T, const RawView& R, uint64_t a, uint64_t b) {
+// Extreme Byte Search over [a, b) with the running maxima (equals range_max)
+CDC_HD uint32_t range_max_t(const SumView& S, const PreSuf& V, const RawView& R, uint64_t a, uint64_t b) {
     const uint64_t ba = a >> 6, bl = (b - 1) >> 6;
     if (ba == bl) return range_max(S, R, a, b);
     const uint64_t fb = (a + 63) >> 6, lb = b >> 6;
-    uint32_t M = fb < lb ? whole_max(S, T, fb, lb) : 0;
+    uint32_t M = fb < lb ? whole_max(S, V, fb, lb) : 0;
     if (M == 255) return 255;
     if ((a & 63) && S.m(ba) > M) {
         const uint32_t h = raw_max(R, a, (ba + 1) << 6);
@@ -412,7 +413,7 @@ CDC_HD uint32_t range_max_t(const SumView& S, const TView& T, const RawView& R, 
 
 // RAM next(s) (equals next_ram). *nat: the cut is natural (a byte >= the
 // window maximum was found), then *val is that byte.
-CDC_HD uint64_t next_ram_t(const SumView& S, const TView& T, const RawView& R, const Prm& P, uint64_t fhi,
+CDC_HD uint64_t next_ram_t(const SumView& S, const PreSuf& T, const RawView& R, const Prm& P, uint64_t fhi,
                            uint64_t s, bool* nat, uint32_t* val) {
     *nat = false;
     if (fhi - s <= P.w) return fhi;
@@ -438,7 +439,7 @@ CDC_HD uint64_t next_ram_t(const SumView& S, const TView& T, const RawView& R, c
 // next_ae): before scanning a target's window for a greater byte, the table
 // tells whether the window holds one at all. *nat: the cut ends a target's
 // window, then *val is the target's byte.
-CDC_HD uint64_t next_ae_t(const SumView& S, const TView& T, const RawView& R, const Prm& P, uint64_t fhi,
+CDC_HD uint64_t next_ae_t(const SumView& S, const PreSuf& T, const RawView& R, const Prm& P, uint64_t fhi,
                           uint64_t s, bool* nat, uint32_t* val) {
     *nat = false;
     const uint64_t limit = umin64(fhi, s + P.mx);
@@ -527,7 +528,7 @@ CDC_HD uint64_t next_ae_t(const SumView& S, const TView& T, const RawView& R, co
 // (the scan that found it already compared it with the whole window); only
 // forced cuts and the end of a quiet run take the full test.
 template <int RULE>
-CDC_HD uint64_t cand_next_t(const SumView& S, const TView& T, const RawView& R, const Prm& P, uint64_t lo,
+CDC_HD uint64_t cand_next_t(const SumView& S, const PreSuf& T, const RawView& R, const Prm& P, uint64_t lo,
                             uint64_t hi, uint64_t y, uint32_t* n) {
     uint64_t s = y;
     uint32_t c = 0;
@@ -588,7 +589,7 @@ CDC_HD uint64_t cand_next_t(const SumView& S, const TView& T, const RawView& R, 
 template <int RULE>
 CDC_HD uint64_t cand_next(const SumView& S, const RawView& R, const Prm& P, uint64_t lo, uint64_t hi, uint64_t y,
                           uint32_t* n) {
-    const TView T{nullptr, 0xFFFFFFFFu, 0, 0};
+    const PreSuf T{nullptr, nullptr};
     return cand_next_t<RULE>(S, T, R, P, lo, hi, y, n);
 }
 
@@ -678,10 +679,10 @@ CDC_HD uint32_t list_next(const CandList& L, const WMax& wmax, const RawView& R,
     return y - 1 < cend ? k : LIST_GENERIC;
 }
 
-// window maximum over the block summaries (and a table, if any)
+// window maximum over the block summaries (and running maxima, if any)
 struct WMaxSum {
     const SumView* S;
-    const TView* T;
+    const PreSuf* T;
     const RawView* R;
     CDC_HD uint32_t operator()(uint64_t a, uint64_t b) const { return range_max_t(*S, *T, *R, a, b); }
 };

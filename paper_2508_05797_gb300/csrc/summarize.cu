@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(S1_THREADS) k_summary_max(SumLaunch a) {
         }
     }
     const uint32_t inv = INV ? 0xFFFFFFFFu : 0u;
+    __shared__ unsigned int wmx[S1_STAGES][S1_THREADS / 32];  // per warp of a tile: its blocks' maximum
     uint32_t i = 0;
     for (uint64_t t = blockIdx.x; t < ntiles; t += g, i++) {
         const int s = i % S1_STAGES;
@@ -140,6 +141,32 @@ __global__ void __launch_bounds__(S1_THREADS) k_summary_max(SumLaunch a) {
             // 64 blocks (two warps) per 4 KiB superblock
             const uint32_t wm = __reduce_max_sync(FULL, M);
             if ((tid & 31) == 0 && wm) atomicMax(&supmax[s][lb >> 6], wm);
+            if (a.spre) {
+                // running maxima inside the superblock: warp scans here, the
+                // other warp's maximum joined after the barrier below
+                const int lane = tid & 31;
+                uint32_t pf = M, sf = M;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t u = __shfl_up_sync(FULL, pf, d), v = __shfl_down_sync(FULL, sf, d);
+                    if (lane >= d) pf = pf > u ? pf : u;
+                    if (lane + d < 32) sf = sf > v ? sf : v;
+                }
+                if (lane == 0) wmx[s][tid >> 5] = wm;
+                __syncthreads();
+                const int wv = tid >> 5;
+                if (wv & 1) {
+                    const uint32_t o = wmx[s][wv - 1];
+                    pf = pf > o ? pf : o;
+                } else {
+                    const uint32_t o = wmx[s][wv + 1];
+                    sf = sf > o ? sf : o;
+                }
+                if (b < a.nblk) {
+                    a.spre[b] = (uint8_t)pf;
+                    a.ssuf[b] = (uint8_t)sf;
+                }
+            }
         }
         __syncthreads();  // every thread is done with stage s
         if (tid < S1_TILE / 4096) {

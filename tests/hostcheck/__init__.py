@@ -45,11 +45,9 @@ def load():
         lib.hc_cand_next.restype = u64
         lib.hc_graph_chain.argtypes = gargs + [vp, u64]
         lib.hc_graph_chain.restype = u64
-        lib.hc_graph_chain_t.argtypes = gargs + [vp, u32, u64, u64, vp, u64]
+        lib.hc_graph_chain_t.argtypes = gargs + [vp, vp, vp, u64]
         lib.hc_graph_chain_t.restype = u64
         lib.hc_list_check.argtypes = gargs + [vp, vp, u32, u64, vp]
         lib.hc_list_check.restype = u64
-        lib.hc_tview_level.argtypes = [u32]
-        lib.hc_tview_level.restype = u32
         _lib = lib
         return lib

@@ -169,16 +169,15 @@ extern "C" uint64_t hc_graph_chain(int rule, const uint8_t* base, const uint8_t*
     });
 }
 
-// the graph's chain with a window-maximum table t (t[b] = max of blocks
-// [b, b + 2^lev), valid for b in [tb0, tb1))
+// the graph's chain with the running maxima inside superblocks (pre, suf)
 extern "C" uint64_t hc_graph_chain_t(int rule, const uint8_t* base, const uint8_t* smax, const uint8_t* sarg,
                                      const uint8_t* sup, uint32_t inv, uint32_t w, uint32_t mn, uint32_t mx,
-                                     uint64_t lo, uint64_t hi, const uint8_t* tt, uint32_t tlev, uint64_t tb0,
-                                     uint64_t tb1, uint64_t* out, uint64_t cap) {
+                                     uint64_t lo, uint64_t hi, const uint8_t* pre, const uint8_t* suf,
+                                     uint64_t* out, uint64_t cap) {
     SumView S{smax, sarg, nullptr, nullptr, 0, 0, sup};
     RawView R{base, inv};
     Prm P{w, mn, mx};
-    TView T{tt, tlev, tb0, tb1};
+    PreSuf T{pre, suf};
     return with_rule(rule, [&](auto rc) -> uint64_t {
         constexpr int RU = decltype(rc)::value;
         uint64_t y = lo, n = 0;
@@ -203,7 +202,6 @@ extern "C" uint64_t hc_graph_chain_t(int rule, const uint8_t* base, const uint8_
     });
 }
 
-extern "C" uint32_t hc_tview_level(uint32_t w) { return tview_level(w); }
 
 // F of every candidate of [lo, hi) from the whole candidate list (cover = hi):
 // writes the list index or ~0u (the list cannot decide) per candidate, and
@@ -216,7 +214,7 @@ extern "C" uint64_t hc_list_check(int rule, const uint8_t* base, const uint8_t* 
     SumView S{smax, sarg, nullptr, nullptr, 0, 0, sup};
     RawView R{base, inv};
     Prm P{w, mn, mx};
-    TView T{nullptr, 0xFFFFFFFFu, 0, 0};
+    PreSuf T{nullptr, nullptr};
     CandList L{pos, val, n, lbase, hi};
     WMaxSum wm{&S, &T, &R};
     return with_rule(rule, [&](auto rc) -> uint64_t {

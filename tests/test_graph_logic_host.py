@@ -147,39 +147,33 @@ def test_is_cand_matches_enumeration(alg, w):
 
 
 @pytest.mark.parametrize("alg,w,mn,mx", [("ram", 200, 100, 4000), ("ram", 7101, 2048, 65536), ("ae", 700, 128, 8192),
-                                          ("ae", 3000, 2000, 30000), ("ram", 3548, 1024, 32768)])
-def test_graph_chain_with_window_table(alg, w, mn, mx):
-    """The window-maximum table (max of 2^lev blocks from each block) gives the
-    same chain; windows whose whole blocks reach outside the table's valid
-    range fall back to the block summaries."""
+                                          ("ae", 3000, 2000, 30000), ("ram", 3548, 1024, 32768),
+                                          ("ae", 15599, 4096, 131072)])
+def test_graph_chain_with_superblock_maxima(alg, w, mn, mx):
+    """Window maxima from the running maxima inside 4 KiB superblocks (prefix
+    and suffix per block, as the summary kernel writes them) give the same
+    chain as the block-by-block summaries."""
     lib = hostcheck.load()
     orc = oracle.get()
     n = 300_000
-    lev = lib.hc_tview_level(w)
-    assert lev != 0xFFFFFFFF and (1 << lev) <= w // 64 - 1 < (2 << lev)
     for k, (name, data) in enumerate(_datasets(n, seed=w).items()):
         lo = (5 * k + 3) % 64
         ar = Arena(data, lo, alg, w)
         sup = _superblocks(ar, alg)
         nb = ar.smax.size
-        span = 1 << lev
-        m = ar.smax.astype(np.int16)
-        t = np.zeros(nb, dtype=np.uint8)
-        # t[b] = max m[b .. b + span) via cumulative doubling
-        cur = m.copy()
-        for j in range(lev):
-            h = 1 << j
-            nxt = cur.copy()
-            nxt[:-h] = np.maximum(cur[:-h], cur[h:])
-            cur = nxt
-        t[:] = cur.astype(np.uint8)
-        for tb0, tb1 in ((0, nb - span), (nb // 3, nb // 2)):  # full table, and a partial one
-            base, sm, sa = ar.ptrs()
-            exp = orc.chunk(alg, data, w, mn, mx)
-            out = np.zeros(exp.size + 8, dtype=np.uint64)
-            got = lib.hc_graph_chain_t(ALG_RULE[alg][0], base, sm, sa, sup.ctypes.data, ar.inv, w, mn, mx, lo, lo + n,
-                                       t.ctypes.data, lev, tb0, tb1, out.ctypes.data, out.size)
-            assert got == exp.size and np.array_equal(out[:got], exp), (alg, name, tb0, tb1)
+        m = ar.smax.copy()
+        pre = np.zeros(nb + 64, dtype=np.uint8)
+        suf = np.zeros(nb + 64, dtype=np.uint8)
+        for q0 in range(0, nb, 64):
+            blk = m[q0:q0 + 64]
+            pre[q0:q0 + blk.size] = np.maximum.accumulate(blk)
+            suf[q0:q0 + blk.size] = np.maximum.accumulate(blk[::-1])[::-1]
+        base, sm, sa = ar.ptrs()
+        exp = orc.chunk(alg, data, w, mn, mx)
+        out = np.zeros(exp.size + 8, dtype=np.uint64)
+        got = lib.hc_graph_chain_t(ALG_RULE[alg][0], base, sm, sa, sup.ctypes.data, ar.inv, w, mn, mx, lo, lo + n,
+                                   pre.ctypes.data, suf.ctypes.data, out.ctypes.data, out.size)
+        assert got == exp.size and np.array_equal(out[:got], exp), (alg, name)
 
 
 @pytest.mark.parametrize("alg,w,mn,mx", CASES)
