@@ -60,7 +60,9 @@ def peaks():
 
 SPEC_SOURCES = ("paper_2508_05797_gb300/csrc/chain.cu", "paper_2508_05797_gb300/csrc/chain_logic.cuh",
                 "paper_2508_05797_gb300/csrc/warp_rules.cuh", "paper_2508_05797_gb300/csrc/cdc_device.cuh")
-SPEC_PROFILE = os.path.join("profiles", "k_spec_mixed_4gib.md")
+# machine-written record of the speculation kernel's DRAM traffic (written by
+# `bench.py --write-traffic` from an ncu capture's CSV)
+SPEC_TRAFFIC = os.path.join("profiles", "k_spec_traffic.json")
 
 
 def sources_sha(paths) -> str:
@@ -72,22 +74,18 @@ def sources_sha(paths) -> str:
 
 
 def profile_traffic():
-    """DRAM bytes per input byte of the speculation kernel, from the committed
-    ncu summary, if that summary was taken on the current kernel sources."""
-    p = os.path.join(ROOT, SPEC_PROFILE)
+    """DRAM bytes per input byte of the speculation kernel from the capture
+    record, if that record was taken on the current kernel sources."""
+    p = os.path.join(ROOT, SPEC_TRAFFIC)
     if not os.path.exists(p):
         return None
-    vals = {}
     with open(p) as f:
-        for line in f:
-            if ":" in line and line.startswith("- "):
-                k, v = line[2:].split(":", 1)
-                vals[k.strip()] = v.strip().strip("`")
-    if vals.get("source_sha256_16") != sources_sha(SPEC_SOURCES):
+        rec = json.load(f)
+    if rec.get("source_sha256_16") != sources_sha(SPEC_SOURCES):
         return None
     try:
-        return float(vals["dram_bytes_per_input_byte"])
-    except (KeyError, ValueError):
+        return float(rec["dram_bytes_per_input_byte"])
+    except (KeyError, TypeError, ValueError):
         return None
 
 
@@ -181,19 +179,118 @@ def allreduce_max(x: float, world: int) -> float:
     return float(t.item())
 
 
-def cpu_baseline(sample_bytes: int = 256 * MIB):
-    """The oracle, single-threaded on a host core, over the first sample_bytes
-    of the stream for all nine (algorithm, mean) pairs."""
+def write_traffic(csv_path: str, input_bytes: int, command: str):
+    """Write SPEC_TRAFFIC from an ncu CSV (metrics dram__bytes_read.sum,
+    dram__bytes_write.sum, gpu__time_duration.sum) of k_spec launches that
+    each chunked `input_bytes` bytes: DRAM bytes per input byte per launch and
+    their mean, with the hash of the kernel sources they were taken on."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hdr = None
+    per = {}
+    for r in rows:
+        if r and r[0] == "ID":
+            hdr = r
+            continue
+        if not hdr or len(r) != len(hdr):
+            continue
+        d = dict(zip(hdr, r))
+        if "k_spec" not in d["Kernel Name"]:
+            continue
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1, "us": 1e3, "ms": 1e6}
+        v = float(d["Metric Value"].replace(",", "")) * scale.get(d["Metric Unit"], 1)
+        per.setdefault(d["ID"], {"kernel": d["Kernel Name"]})[d["Metric Name"]] = v
+    launches = []
+    for k, d in sorted(per.items(), key=lambda x: int(x[0])):
+        b = d.get("dram__bytes_read.sum", 0.0) + d.get("dram__bytes_write.sum", 0.0)
+        launches.append({"kernel": d["kernel"], "dram_bytes": int(b), "dram_bytes_per_input_byte": b / input_bytes,
+                         "time_ns": d.get("gpu__time_duration.sum")})
+    if not launches:
+        raise SystemExit("no k_spec launches in %s" % csv_path)
+    rec = {"kernel": "k_spec", "input_bytes_per_launch": input_bytes, "launches": launches,
+           "dram_bytes_per_input_byte": sum(x["dram_bytes_per_input_byte"] for x in launches) / len(launches),
+           "source_sha256_16": sources_sha(SPEC_SOURCES), "command": command,
+           "note": "times under ncu are serialised and cold; only the byte counts are used"}
+    with open(os.path.join(ROOT, SPEC_TRAFFIC), "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec))
+
+
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm part)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model Name", "Hardware"):
+        for line in txt.splitlines():
+            if line.startswith(key) and ":" in line:
+                return line.split(":", 1)[1].strip()
+    parts = {line.split(":", 1)[1].strip() for line in txt.splitlines()
+             if line.startswith("CPU part") and ":" in line}
+    impl = {line.split(":", 1)[1].strip() for line in txt.splitlines()
+            if line.startswith("CPU implementer") and ":" in line}
+    if parts:
+        return "Arm implementer %s part %s" % (",".join(sorted(impl)), ",".join(sorted(parts)))
+    return "unknown"
+
+
+def cpu_baseline(sample_bytes: int = 128 * MIB):
+    """The oracle on the host cores: each of the nine (algorithm, mean) jobs on
+    one thread over the first sample_bytes of the stream (the chunk chain is
+    sequential), then all nine at once (one thread each), and a sample of the
+    batched files (log-normal sizes, seed 3) spread over every core."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+
     import oracle
     import synth
+    cores = os.cpu_count() or 1
     data = synth.mixed_range(1, STREAM_LEN, 0, sample_bytes)
+    cfg = configs()
+    single = []
     t0 = time.perf_counter()
-    for alg, mean, w, mn, mx in configs():
+    for alg, mean, w, mn, mx in cfg:
+        t1 = time.perf_counter()
         oracle.count(alg, data, w, mn, mx)
-    dt = time.perf_counter() - t0
-    return {"value": round(9 * sample_bytes / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "first %d MiB of the 4 GiB mixed stream, all 9 (alg, mean) pairs, one thread" % (
-                sample_bytes // MIB), "seconds": round(dt, 2)}
+        single.append(sample_bytes / (time.perf_counter() - t1) / 1e9)
+    dt_single = time.perf_counter() - t0
+    # all nine jobs at once (the oracle's C loop releases the GIL)
+    with ThreadPoolExecutor(min(len(cfg), cores)) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(lambda c: oracle.count(c[0], data, c[2], c[3], c[4]), cfg))
+        dt_par = time.perf_counter() - t0
+    # files: log-normal sizes (median 64 KiB), RAM and MAXP at 8 KiB mean, over all cores
+    sizes = synth.lognormal_sizes(3, 4000, 65536, 1.5, 1, 8 * MIB).astype(np.int64)
+    off = np.zeros(sizes.size + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    arena = synth.mixed(3, int(off[-1]))
+    t = wtable()["mixed_4g_seed1"]
+    jobs = [(a, i) for a in ("maxp", "ram") for i in range(sizes.size)]
+
+    def file_job(j):
+        a, i = j
+        e = t[a]["8192"]
+        return oracle.count(a, arena[off[i]:off[i + 1]], e["w"], e["min"], e["max"])
+
+    with ThreadPoolExecutor(cores) as ex:
+        t0 = time.perf_counter()
+        list(ex.map(file_job, jobs))
+        dt_files = time.perf_counter() - t0
+    return {"value": round(len(cfg) * sample_bytes / dt_single / 1e9, 4), "unit": "GB/s", "cores": 1,
+            "kind": "oracle",
+            "sample": "first %d MiB of the 4 GiB mixed stream, each of the 9 (alg, mean) pairs on one thread" % (
+                sample_bytes // MIB),
+            "seconds": round(dt_single, 2), "per_job_GBps": [round(x, 4) for x in single],
+            "host": {"hardware_concurrency": cores, "cpu_model": cpu_model()},
+            "all_jobs_parallel": {"value": round(len(cfg) * sample_bytes / dt_par / 1e9, 4), "unit": "GB/s",
+                                  "cores": min(len(cfg), cores), "seconds": round(dt_par, 2)},
+            "files_all_cores": {"value": round(2 * int(off[-1]) / dt_files / 1e9, 4), "unit": "GB/s",
+                                "cores": cores, "seconds": round(dt_files, 2),
+                                "sample": "%d files (log-normal, median 64 KiB, seed 3, %.1f MB), MAXP and RAM at "
+                                          "8 KiB mean" % (sizes.size, off[-1] / 1e6)}}
 
 
 def batched_workload(dev, n_files: int = 100_000, warmup: int = 2, reps: int = 3):
@@ -456,25 +553,39 @@ def dedup_workload(dev, base_bytes: int = GIB, n_versions: int = 15, reps: int =
 
 
 def small_workload(dev, copies: int = 16, reps: int = 5):
-    """Single 16 MiB buffers of uniform bytes (seed 0) chunked with RAM, AE and
-    MAXP at 8 KiB mean (windows from the calibrated table). A call this small is
-    bound by the latency of its kernel sequence, not by HBM: 16 calls on 16
-    copies of the buffer (256 MiB, more than L2) are captured in one CUDA graph,
-    replayed, and the time per call is the replay time / 16."""
-    import numpy as np
+    """Single 16 MiB buffers chunked with RAM, AE and MAXP at 8 KiB mean:
+    uniform bytes (seed 0, windows calibrated on them) and the first 16 MiB of
+    the mixed stream. A call this small is bound by the latency of its kernel
+    sequence, not by HBM: 16 calls on 16 copies of the buffer (256 MiB, more
+    than L2) are captured in one CUDA graph, replayed, and the time per call is
+    the replay time / 16."""
     import torch
 
     import synth
-    from paper_2508_05797_gb300 import Chunker
 
     n = 16 * MIB
-    t = wtable()["uniform_16m_seed0"]
-    buf = torch.from_numpy(synth.uniform(0, n)).to(dev)
+    res = {"workload": "16 MiB buffers, one call per buffer; %d calls on %d copies in one CUDA graph, "
+                       "time per call = replay time / %d; `uniform`: uniform bytes (seed 0, windows calibrated on "
+                       "them), `mixed_prefix`: the first 16 MiB of the 4 GiB mixed stream" % (copies, copies, copies)}
+    res["uniform"] = _small_calls(dev, torch.from_numpy(synth.uniform(0, n)), wtable()["uniform_16m_seed0"],
+                                  copies, reps)
+    res["mixed_prefix"] = _small_calls(dev, torch.from_numpy(synth.mixed_range(1, STREAM_LEN, 0, n)),
+                                       wtable()["mixed_4g_seed1"], copies, reps)
+    torch.cuda.empty_cache()
+    return res
+
+
+def _small_calls(dev, host_buf, t, copies, reps):
+    import torch
+
+    from paper_2508_05797_gb300 import Chunker
+
+    n = host_buf.numel()
+    buf = host_buf.to(dev)
     ds = [buf.clone() for _ in range(copies)]
     del buf
     s = torch.cuda.Stream(dev)
-    res = {"workload": "uniform 16 MiB (seed 0), one call per buffer; %d calls on %d copies in one CUDA graph, "
-                       "time per call = replay time / %d" % (copies, copies, copies)}
+    res = {}
     peak, _ = peaks()
     for alg in ALGS:
         e = t[alg]["8192"]
@@ -511,11 +622,11 @@ def small_workload(dev, copies: int = 16, reps: int = 5):
             raise RuntimeError("small workload: copies of one buffer gave different boundary counts")
         ms = statistics.median(ts)
         res[alg] = {"us_per_call": round(ms * 1e3, 1), "GBps": round(n / (ms / 1e3) / 1e9, 1),
-                    "hbm_frac": round(n / (ms / 1e3) / 1e9 / peak, 4), "boundaries": counts.pop(), "w": w}
+                    "hbm_frac": round(n / (ms / 1e3) / 1e9 / peak, 4), "boundaries": counts.pop(), "w": w,
+                    "launches_per_call": ck.last_launches()}
         del g
         ck.close()
     del ds
-    torch.cuda.empty_cache()
     return res
 
 
@@ -625,7 +736,15 @@ def main():
     ap.add_argument("--means", default=",".join(map(str, MEANS)), help="subset of 4096,8192,16384")
     ap.add_argument("--len-mib", type=int, default=STREAM_LEN // MIB,
                     help="stream length (a prefix of the 4 GiB stream; profiling cases)")
+    ap.add_argument("--pipeline", type=int, default=0,
+                    help="chain stage: 0 automatic, 1 speculative segments, 2 candidate graph (profiling cases)")
+    ap.add_argument("--write-traffic", metavar="CSV",
+                    help="write the k_spec DRAM-traffic record from an ncu CSV of a --len-mib run and exit")
+    ap.add_argument("--traffic-command", default="", help="the ncu command that made the CSV (recorded)")
     args = ap.parse_args()
+    if args.write_traffic:
+        write_traffic(args.write_traffic, args.len_mib * MIB, args.traffic_command)
+        return 0
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         return run_reference(args, rank, world)
@@ -647,8 +766,10 @@ def main():
     cfg = configs(tuple(args.algs.split(",")), tuple(int(x) for x in args.means.split(",")))
     ncfg = len(cfg)
     handles, outs, counts = [], [], []
+    from paper_2508_05797_gb300.cdc import OPT_PIPELINE
     for alg, mean, w, mn, mx in cfg:
         ck = Chunker(local)
+        ck.set_option(OPT_PIPELINE, args.pipeline)
         ck.reserve(alg, w, mn, mx, n)
         handles.append(ck)
         outs.append(torch.empty(n // mn + 1, dtype=torch.int64, device=dev))
@@ -738,22 +859,33 @@ def main():
                         "chain_ms": [round(r["chain_ms"], 4) for r in rows],
                         "spec_ms": [round(r["spec_ms"], 4) for r in rows]}
     # roofline of the dominant kernel, k_spec (the speculation kernel of the
-    # chain stage): algorithmic bytes = the input bytes one launch chunks;
-    # launch times from the timed region (three streams overlap, so other
-    # calls' kernels share the GPU during a launch) and from the calls alone
+    # chain stage): algorithmic bytes = the input bytes one launch chunks
+    # (the chain stage's one pass over the stream); its launch times from the
+    # calls alone on one stream (no other call's kernels on the GPU during a
+    # launch), and from the timed region for comparison (three streams overlap
+    # there). k_spec is bound by the latency of dependent chain steps, not by
+    # DRAM (its own DRAM traffic, `traffic`, is under 0.1 byte per input
+    # byte); the block-summary kernel is the one that streams every byte.
     spec_avg_ms = spec_ms_total / max(1, spec_calls)
-    achieved = n / (spec_avg_ms / 1e3) / 1e9
+    achieved_tr = n / (spec_avg_ms / 1e3) / 1e9
     iso_spec_ms = sum(r["spec_ms"] for r in iso) / max(1, len(iso))
     iso_achieved = n / (iso_spec_ms / 1e3) / 1e9
+    iso_sum_ms = sum(r["summary_ms"] for r in iso) / max(1, len(iso))
+    sum_achieved = n / (iso_sum_ms / 1e3) / 1e9
     dpb = profile_traffic()
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": int(dpb * n) if dpb is not None else None,
+    roofline = {"bound": "hbm", "achieved": round(iso_achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(iso_achieved / peak, 4), "traffic": int(dpb * n) if dpb is not None else None,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-                "kernel": "k_spec (chain stage: speculative chains + stitching)",
-                "algorithmic_bytes_per_launch": n, "avg_launch_ms": round(spec_avg_ms, 4),
-                "launches_overlap": "timed region: the step's nine calls run on %d streams" % nstreams,
-                "alone": {"achieved": round(iso_achieved, 1), "frac": round(iso_achieved / peak, 4),
-                          "avg_launch_ms": round(iso_spec_ms, 4)}}
+                "kernel": "k_spec (chain stage: speculative chains), the largest share of the step's device time",
+                "algorithmic_bytes_per_launch": n, "avg_launch_ms": round(iso_spec_ms, 4),
+                "launch_times": "each call alone on one stream, CUDA events around the kernel",
+                "limited_by": "latency of dependent chain steps (its DRAM traffic is `traffic`)",
+                "timed_region": {"achieved": round(achieved_tr, 1), "frac": round(achieved_tr / peak, 4),
+                                 "avg_launch_ms": round(spec_avg_ms, 4),
+                                 "note": "the step's nine calls overlap on %d streams" % nstreams},
+                "summary_kernel": {"kernel": "k_summary_max / k_summary_maxp (block summaries: reads every byte)",
+                                   "achieved": round(sum_achieved, 1), "frac": round(sum_achieved / peak, 4),
+                                   "avg_launch_ms": round(iso_sum_ms, 4)}}
     line = {"metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded)",

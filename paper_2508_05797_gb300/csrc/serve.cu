@@ -4,13 +4,15 @@
 //
 // A worker thread owns `slots` execution slots; each has a CUDA stream, a
 // library handle (its workspace stays on the device between batches), a device
-// arena for request bytes and a pinned staging area for offsets and
-// boundaries. Requests become eligible at their arrival time. Whenever a slot
-// is free, the worker packs the eligible requests that share the oldest one's
-// algorithm and parameters (oldest first, up to the slot's capacity) into one
-// batch: one host-to-device copy per request into the arena, one batched
-// chunking call over the packed files, one copy of the boundary index and
-// boundaries back, one event. Requests that arrive while slots are busy wait
+// arena for request bytes and a pinned staging area for offsets, copy
+// descriptors and boundaries. Requests become eligible at their arrival time.
+// Whenever a slot is free, the worker packs the eligible requests that share
+// the oldest one's algorithm and parameters (oldest first, up to the slot's
+// capacity) into one batch: requests in page-locked host memory (which the
+// device reads directly) are listed as pieces of at most 64 KiB and brought in
+// by one gather kernel; others take one host-to-device copy each; then one
+// batched chunking call over the packed files, one copy of the boundary index
+// and boundaries back, one event. Requests that arrive while slots are busy wait
 // and join the next batch of their kind; batches on different slots overlap on
 // the device (copies and kernels on separate streams). When a slot's event
 // completes, the worker hands each request its boundaries and timestamps.
@@ -34,10 +36,59 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// One piece of a request to bring into the arena: `len` bytes (<= kPiece)
+// from the device-addressable host address `src` to arena offset `dst`.
+struct GatherPiece {
+    const uint8_t* src;
+    uint64_t dst;
+    uint64_t len;
+};
+constexpr uint64_t kPiece = 64u << 10;
+constexpr int kGatherThreads = 256;
+
+// One CTA per piece: the destination's 16-byte granules inside the piece are
+// stored whole (two aligned 16-byte loads of the source, funnel-shifted into
+// place), the partial granules at its two ends byte by byte.
+__global__ void __launch_bounds__(kGatherThreads) k_gather(const GatherPiece* pieces, uint32_t n, uint8_t* arena) {
+    for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const GatherPiece pc = pieces[i];
+        const uint64_t d0 = pc.dst, d1 = pc.dst + pc.len;
+        const uint64_t a0 = (d0 + 15) & ~15ull, a1 = d1 & ~15ull;  // whole granules [a0, a1)
+        if (a0 >= a1) {
+            for (uint64_t d = d0 + threadIdx.x; d < d1; d += kGatherThreads) arena[d] = pc.src[d - d0];
+            continue;
+        }
+        for (uint64_t d = d0 + threadIdx.x; d < a0; d += kGatherThreads) arena[d] = pc.src[d - d0];
+        for (uint64_t d = a1 + threadIdx.x; d < d1; d += kGatherThreads) arena[d] = pc.src[d - d0];
+        for (uint64_t g = a0 + 16ull * threadIdx.x; g < a1; g += 16ull * kGatherThreads) {
+            const uintptr_t sp = reinterpret_cast<uintptr_t>(pc.src) + (g - d0);
+            const uint32_t sh = (uint32_t)(sp & 15);
+            const uint4* q = reinterpret_cast<const uint4*>(sp - sh);
+            const uint4 x = q[0];
+            uint4 o;
+            if (sh == 0) {
+                o = x;
+            } else {
+                // the second granule holds the rest of this one's bytes, so it
+                // lies in the source's pages
+                const uint4 y = q[1];
+                const uint32_t wv[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+                const uint32_t k = sh >> 2, r = 8 * (sh & 3);
+                uint32_t ov[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) ov[j] = __funnelshift_r(wv[k + j], wv[k + j + 1], r);
+                o = make_uint4(ov[0], ov[1], ov[2], ov[3]);
+            }
+            *reinterpret_cast<uint4*>(arena + g) = o;
+        }
+    }
+}
+
 struct Request {
     cdc_alg alg;
     cdc_params p;
     const uint8_t* data;
+    const uint8_t* dev_src;  // the same bytes as the device addresses them (page-locked), or null
     size_t len;
     uint64_t* bounds;
     size_t capacity;
@@ -54,6 +105,9 @@ struct Slot {
     uint64_t* d_bounds = nullptr;  // boundaries
     uint64_t* d_index = nullptr;   // per-file boundary index (max_files + 1)
     uint64_t* h_off = nullptr;     // pinned staging
+    GatherPiece* h_pieces = nullptr;  // pinned: copy descriptors of the batch
+    GatherPiece* d_pieces = nullptr;
+    size_t pieces_cap = 0;
     uint64_t* h_index = nullptr;
     uint64_t* h_bounds = nullptr;
     size_t bounds_cap = 0;
@@ -98,6 +152,8 @@ static void slot_free(Slot& s) {
     cudaFree(s.d_bounds);
     cudaFree(s.d_index);
     if (s.h_off) cudaFreeHost(s.h_off);
+    if (s.h_pieces) cudaFreeHost(s.h_pieces);
+    cudaFree(s.d_pieces);
     if (s.h_index) cudaFreeHost(s.h_index);
     if (s.h_bounds) cudaFreeHost(s.h_bounds);
     if (s.stream) cudaStreamDestroy(s.stream);
@@ -134,13 +190,27 @@ bool cdc_server_s::launch(Slot& s, std::deque<Request>& pending, double now) {
     if (s.batch.empty()) return false;
     const size_t n = s.batch.size();
     s.h_off[0] = 0;
+    size_t np = 0;  // gather pieces
     for (size_t i = 0; i < n; i++) {
         Request& r = s.batch[i];
         r.t_start = now;
         s.h_off[i + 1] = s.h_off[i] + r.len;
-        if (r.len && cudaMemcpyAsync(s.arena + s.h_off[i], r.data, r.len, cudaMemcpyHostToDevice, s.stream) !=
-                         cudaSuccess)
+        if (!r.len) continue;
+        if (r.dev_src && np + (r.len + kPiece - 1) / kPiece <= s.pieces_cap) {
+            for (uint64_t o = 0; o < r.len; o += kPiece)
+                s.h_pieces[np++] = GatherPiece{r.dev_src + o, s.h_off[i] + o, std::min<uint64_t>(kPiece, r.len - o)};
+        } else if (cudaMemcpyAsync(s.arena + s.h_off[i], r.data, r.len, cudaMemcpyHostToDevice, s.stream) !=
+                   cudaSuccess) {
             fatal = CDC_ERR_CUDA;
+        }
+    }
+    if (np) {
+        if (cudaMemcpyAsync(s.d_pieces, s.h_pieces, np * sizeof(GatherPiece), cudaMemcpyHostToDevice, s.stream) !=
+            cudaSuccess)
+            fatal = CDC_ERR_CUDA;
+        const unsigned grid = (unsigned)std::min<size_t>(np, 65535);
+        k_gather<<<grid, kGatherThreads, 0, s.stream>>>(s.d_pieces, (uint32_t)np, s.arena);
+        if (cudaGetLastError() != cudaSuccess) fatal = CDC_ERR_CUDA;
     }
     if (cudaMemcpyAsync(s.d_off, s.h_off, (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, s.stream) != cudaSuccess)
         fatal = CDC_ERR_CUDA;
@@ -279,8 +349,10 @@ extern "C" cdc_status cdc_server_create(cdc_server* out, int device, size_t budg
     s->slot_bytes = arena & ~(size_t)255;
     s->slots.resize((size_t)slots);
     const size_t bcap = s->slot_bytes / 1024 + s->max_files + 1;  // boundaries per batch
+    const size_t pcap = s->slot_bytes / kPiece + s->max_files + 1;  // gather pieces per batch
     for (Slot& sl : s->slots) {
         sl.bounds_cap = bcap;
+        sl.pieces_cap = pcap;
         bool ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess &&
                   cdc_create(&sl.h, device) == CDC_OK && cudaMalloc(&sl.arena, s->slot_bytes) == cudaSuccess &&
@@ -288,6 +360,8 @@ extern "C" cdc_status cdc_server_create(cdc_server* out, int device, size_t budg
                   cudaMalloc(&sl.d_index, (s->max_files + 1) * sizeof(uint64_t)) == cudaSuccess &&
                   cudaMalloc(&sl.d_bounds, bcap * sizeof(uint64_t)) == cudaSuccess &&
                   cudaMallocHost(&sl.h_off, (s->max_files + 1) * sizeof(uint64_t)) == cudaSuccess &&
+                  cudaMallocHost(&sl.h_pieces, pcap * sizeof(GatherPiece)) == cudaSuccess &&
+                  cudaMalloc(&sl.d_pieces, pcap * sizeof(GatherPiece)) == cudaSuccess &&
                   cudaMallocHost(&sl.h_index, (s->max_files + 1) * sizeof(uint64_t)) == cudaSuccess &&
                   cudaMallocHost(&sl.h_bounds, bcap * sizeof(uint64_t)) == cudaSuccess;
         // the workspace for a full slot, so batches do not allocate
@@ -315,6 +389,17 @@ extern "C" cdc_status cdc_server_submit(cdc_server s, cdc_alg alg, cdc_params p,
     r.alg = alg;
     r.p = p;
     r.data = host_data;
+    r.dev_src = nullptr;
+    if (len) {
+        // page-locked host memory: the device reads it directly (one gather
+        // kernel per batch instead of a copy call per request)
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, host_data) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+            at.devicePointer)
+            r.dev_src = static_cast<const uint8_t*>(at.devicePointer);
+        else
+            cudaGetLastError();
+    }
     r.len = len;
     r.bounds = host_bounds;
     r.capacity = capacity;
