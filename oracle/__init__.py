@@ -120,12 +120,16 @@ class Oracle:
 
     def byte_shares(self, alg, data, w: int, mn: int, mx: int):
         """(bytes read by Extreme Byte Searches, bytes read by Range Scans)
-        while the whole buffer is chunked, as Section 3.3 composes RAM and AE;
-        None for MAXP or AE with min > w + 1 (undefined there)."""
+        while the whole buffer is chunked, as Section 3.3 composes the
+        algorithms; None for AE with min > w + 1 (undefined there). The MAXP
+        procedure checks each of its cuts against next() and raises if one
+        differs."""
         a = self._buf(data)
         e, r = ctypes.c_uint64(0), ctypes.c_uint64(0)
         st = self.lib.oracle_byte_shares(alg_id(alg), a.ctypes.data if a.size else None, a.size, w, mn, mx,
                                          ctypes.byref(e), ctypes.byref(r))
+        if st == -2:
+            raise AssertionError("MAXP share procedure cut differs from next()")
         return None if st else (int(e.value), int(r.value))
 
     def horizon(self, alg, w: int, mx: int) -> int:

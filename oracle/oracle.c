@@ -188,16 +188,59 @@ uint64_t oracle_rs(int cmp, const uint8_t* B, uint64_t len, uint64_t a, uint64_t
  *        finds the next target (the bytes after the target up to it) and the
  *        search repeats; otherwise the chunk ends after the window. Defined
  *        for min <= w + 1, where the window end is always a permitted cut.
- * Adds to *ebs and *rs; returns 0, or -1 for MAXP or AE with min > w + 1. */
+ *   MAXP: Range Scans with the GT comparator, each followed by two Extreme
+ *        Byte Searches (Section 3.3), from p = max(s + min - 1, w) (the first
+ *        position that may end the chunk with both windows inside the data):
+ *        a search over the left window [p - w, p) gives its maximum L and the
+ *        last position m holding it; every position up to m + w still has m
+ *        in its left window, so a GT scan for a byte above L over
+ *        [p, min(m + w + 1, end)) finds the first of them that beats its own
+ *        left window (end = min(L_chunk, len - w)); if it finds one (q), a
+ *        search over the right window (q, q + w] decides whether q is a
+ *        target (the chunk ends after it) or the scan goes on from q + 1;
+ *        if it finds none, the scan goes on from its end. Scans read the
+ *        bytes up to and including the one they stop at.
+ * Adds to *ebs and *rs; returns 0, -1 for AE with min > w + 1, or -2 if a
+ * MAXP cut differs from oracle_next (a self-check of the procedure). */
 int oracle_byte_shares(int alg, const uint8_t* B, uint64_t len, uint32_t w, uint32_t mn, uint32_t mx,
                        uint64_t* ebs, uint64_t* rs) {
-    if (alg == OR_MAXP) return -1;
     if ((alg == OR_AE_MAX || alg == OR_AE_MIN) && mn > w + 1) return -1;
     uint64_t s = 0;
     while (s < len) {
         const uint64_t L = umin(len, s + mx);
         uint64_t e;
-        if (alg == OR_RAM) {
+        if (alg == OR_MAXP) {
+            const uint64_t cend = len > w ? umin(L, len - w) : 0;
+            uint64_t p = umax(s + mn - 1, w);
+            e = L;
+            while (p < cend) {
+                uint32_t lmax = 0;
+                uint64_t m = p - w;
+                for (uint64_t i = p - w; i < p; i++)  /* left window: maximum, last position */
+                    if (B[i] >= lmax) {
+                        lmax = B[i];
+                        m = i;
+                    }
+                *ebs += w;
+                const uint64_t stop = umin(cend, m + w + 1);
+                const uint64_t q = oracle_rs(0, B, len, p, stop, lmax);
+                if (q >= stop) {
+                    *rs += stop - p;
+                    p = stop;
+                    continue;
+                }
+                *rs += q - p + 1;
+                uint64_t at;
+                const uint32_t rmax = oracle_ebs(0, B, len, q + 1, q + w + 1, &at);
+                *ebs += w;
+                if (B[q] > rmax) {
+                    e = q + 1;
+                    break;
+                }
+                p = q + 1;
+            }
+            if (e != oracle_next(alg, B, len, s, w, mn, mx)) return -2;
+        } else if (alg == OR_RAM) {
             if (len - s <= w) {
                 *ebs += len - s;
                 e = len;
