@@ -293,6 +293,31 @@ def cpu_baseline(sample_bytes: int = 128 * MIB):
                                           "8 KiB mean" % (sizes.size, off[-1] / 1e6)}}
 
 
+CDF_KIB = (1, 2, 4, 8, 16, 32, 64)
+
+
+def size_cdf(bounds_list, bin_width: int = 1024, n_bins: int = 129):
+    """Chunk-size distribution of one or more boundary lists (int64 CUDA
+    tensors), counted on the device by cdc_size_histogram: the chunk count,
+    the mean size and the CDF at 1..64 KiB (fraction of chunks smaller than
+    each size), the paper's chunk-size CDF (Section 5.2) in a few points."""
+    from paper_2508_05797_gb300 import size_histogram
+    h = None
+    total = 0
+    for b in bounds_list:
+        x = size_histogram(b, bin_width, n_bins)
+        h = x if h is None else h + x
+        total += int(b[-1].item()) if b.numel() else 0
+    h = h.cpu().tolist()
+    n = sum(h)
+    cum, acc = [], 0
+    for c in h:
+        acc += c
+        cum.append(acc)
+    return {"chunks": n, "mean": round(total / max(n, 1), 1),
+            "cdf_below_kib": {str(k): round(cum[k * 1024 // bin_width - 1] / max(n, 1), 4) for k in CDF_KIB}}
+
+
 def batched_workload(dev, n_files: int = 100_000, warmup: int = 2, reps: int = 3):
     """The batched form against a per-file launch loop: files with log-normal
     sizes (median 64 KiB, sigma 1.5, clipped to 1 B .. 256 MiB, seed 3) of
@@ -380,6 +405,17 @@ def batched_workload(dev, n_files: int = 100_000, warmup: int = 2, reps: int = 3
                     "boundaries": int(index[-1])}
         ck.close()
         del out, out2, idx, cnt, g
+    # chunk-size distribution of every algorithm over all files (untimed)
+    res["size_cdf"] = {}
+    ck = Chunker(dev.index)
+    for alg in ("ram", "ae", "ae_min", "maxp"):
+        e = t["ae" if alg == "ae_min" else alg]["8192"]
+        b, ix = ck.chunk_batch(arena, d_off, alg, e["w"], e["min"], e["max"])
+        # boundaries are relative to each file's start: make them arena offsets
+        b = b + torch.repeat_interleave(d_off[:-1], ix[1:] - ix[:-1])
+        res["size_cdf"][alg] = size_cdf([b])
+        del b, ix
+    ck.close()
     del arena
     torch.cuda.empty_cache()
     return res
@@ -488,9 +524,10 @@ def prims_workload(data, dev, n_q: int = 1 << 20, span: int = 8192, reps: int = 
     # byte shares of the two patterns in RAM and AE at 8 KiB mean (cdc_byte_shares
     # over the chunk boundaries of the whole stream)
     from paper_2508_05797_gb300 import byte_shares, chunk
-    shares = {}
-    for alg in ("ram", "ae"):
-        e = wtable()["mixed_4g_seed1"][alg]["8192"]
+    shares = {"paper_context": "Section 5.5 reports RAM 96.70 / 3.30 and MAXP 10.26 / 89.74 (EBS / RS %) on its "
+                               "DEB dataset; these shares are on the synthetic mixed stream"}
+    for alg in ("ram", "ae", "ae_min", "maxp"):
+        e = wtable()["mixed_4g_seed1"]["ae" if alg == "ae_min" else alg]["8192"]
         b = chunk(data, alg, e["w"], e["min"], e["max"])
         byte_shares(data, b, alg, e["w"], e["min"], e["max"])
         torch.cuda.synchronize()
@@ -501,6 +538,11 @@ def prims_workload(data, dev, n_q: int = 1 << 20, span: int = 8192, reps: int = 
         shares[alg] = {"ebs_pct": round(100.0 * es / max(1, es + rb), 2), "rs_pct": round(100.0 * rb / max(1, es + rb), 2),
                        "ebs_bytes": es, "rs_bytes": rb, "ms": round(e0.elapsed_time(e1), 3)}
     out["byte_shares_8k"] = shares
+    # chunk-size distributions of the four algorithms on the whole stream
+    out["size_cdf_8k"] = {}
+    for alg in ("ram", "ae", "ae_min", "maxp"):
+        e = wtable()["mixed_4g_seed1"]["ae" if alg == "ae_min" else alg]["8192"]
+        out["size_cdf_8k"][alg] = size_cdf([chunk(data, alg, e["w"], e["min"], e["max"])])
     return out
 
 
@@ -545,8 +587,15 @@ def dedup_workload(dev, base_bytes: int = GIB, n_versions: int = 15, reps: int =
                     "unique_chunks": rep["unique_chunks"], "unique_ratio": round(rep["unique_chunks"] / rep["chunks"], 5),
                     "savings_pct": round(100 * rep["savings"], 3), "mean_chunk": round(rep["mean_size"], 1),
                     "size_quantiles": rep["size_quantiles"]}
+        res[alg]["size_cdf"] = size_cdf([b for _, b in pieces])
         ck.close()
         del outs, cnts, pieces
+    # the other two algorithms' chunk-size distributions (untimed)
+    for alg in ("ae_min", "maxp"):
+        e = t["ae" if alg == "ae_min" else alg]["8192"]
+        ck = Chunker(dev.index)
+        res.setdefault("size_cdf_other", {})[alg] = size_cdf([ck.chunk(d, alg, e["w"], e["min"], e["max"]) for d in dv])
+        ck.close()
     del dv
     torch.cuda.empty_cache()
     return res

@@ -258,12 +258,21 @@ CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
  * out_bounds, out = number of boundaries; CDC_ERR_CAPACITY with `*n` = the
  * number needed). The call synchronises `stream`.
  *   - len > CDC_STATIC_MAX_LEN returns CDC_ERR_INVALID and enqueues nothing.
+ *   - data and out_bounds must be memory of the current device (or managed
+ *     memory); host memory, pinned or not, and another device's memory
+ *     return CDC_ERR_INVALID and enqueue nothing.
  *   - The first call on a device looks up the scratch array's device address
- *     (the CUDA runtime may load the library's device code at that moment)
- *     and clears the parts that must start at zero: the control block and
- *     the segments' ready flags. Make that first call before any stream
- *     capture starts. Every call also clears the control block's error word
- *     before it launches.
+ *     (the CUDA runtime may load the library's device code at that moment,
+ *     which claims the CDC_STATIC_SCRATCH_BYTES of device memory) and clears
+ *     the parts that must start at zero: the control block and the segments'
+ *     ready flags. Make that first call at start-up, before memory is fully
+ *     claimed and before any stream capture starts. Every call also clears
+ *     the control block's error word before it launches.
+ *   - The call cannot be captured into a CUDA graph: it reads the boundary
+ *     count back to the host and synchronises `stream`.
+ *   - The address is cached per device for the life of the process. A
+ *     device reset (cudaDeviceReset) while the library is loaded is not
+ *     supported: later calls would use the stale address.
  *   - The scratch is shared by every caller on a device: calls that overlap
  *     in time (several host threads, or several streams) race on it and give
  *     wrong results. Serialise them.
@@ -304,10 +313,15 @@ CDC_API cdc_status cdc_rs(cdc_rs_cmp cmp, const uint8_t* data, size_t len, const
  * tail of at most w bytes) and one GEQ scan from max(s + w, s + min - 1) to
  * the cut. AE-Max / AE-Min: per target (a byte beyond every earlier byte of
  * the chunk) one search over the w bytes after it, clipped at the chunk's
- * last byte, and GT / LT scans from target to target. MAXP (the paper does
- * not say where its scans stop) and AE with min > w + 1 (where the window end
- * is not always a permitted cut) give CDC_ERR_INVALID. Asynchronous on
- * `stream`; no handle needed. */
+ * last byte, and GT / LT scans from target to target. MAXP: from
+ * p = max(s + min - 1, w), a search over the left window [p - w, p) gives its
+ * maximum and the last position m holding it; a GT scan from p, stopping at
+ * m + w (where m leaves the window) or at the first byte above that maximum,
+ * reads the bytes up to the one it stops at; a byte it stops at costs one
+ * search over its right window, which decides whether the chunk ends after it
+ * or the scan resumes one byte later. AE with min > w + 1 (where the window
+ * end is not always a permitted cut), w = 0, min = 0 or min > max give
+ * CDC_ERR_INVALID. Asynchronous on `stream`; no handle needed. */
 CDC_API cdc_status cdc_byte_shares(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
                                    const uint64_t* d_bounds, size_t n, uint64_t* d_out, cdc_stream stream);
 
@@ -320,6 +334,16 @@ CDC_API cdc_status cdc_byte_shares(cdc_alg alg, cdc_params p, const uint8_t* dat
  * xxHash3, Section 5). Asynchronous on `stream`. */
 CDC_API cdc_status cdc_fingerprint(const uint8_t* data, size_t len, const uint64_t* d_bounds, size_t n,
                                    uint64_t* d_fp, cdc_stream stream);
+
+/* Chunk-size distribution (the paper plots its CDF per algorithm, Section
+ * 5.2): chunk i of the boundary list d_bounds (n entries, as cdc_chunk writes
+ * them; chunk i is [d_bounds[i-1], d_bounds[i]), d_bounds[-1] = 0) is counted
+ * in bin floor(size / bin_width), sizes of n_bins * bin_width bytes or more in
+ * the last bin. d_hist: n_bins uint64 counters on the device, overwritten.
+ * 1 <= n_bins <= 8192, bin_width >= 1 (else CDC_ERR_INVALID). Asynchronous on
+ * `stream`; no handle needed. */
+CDC_API cdc_status cdc_size_histogram(const uint64_t* d_bounds, size_t n, uint64_t bin_width, uint32_t n_bins,
+                                      uint64_t* d_hist, cdc_stream stream);
 
 /* ---- resumable chunking of a stream that arrives in pieces ----------------
  *

@@ -94,6 +94,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "cdc_rs": ([i32, vp, sz, vp, vp, sz, vp, vp], i32),
             "cdc_fingerprint": ([vp, sz, vp, sz, vp, vp], i32),
             "cdc_byte_shares": ([i32, P, vp, sz, vp, sz, vp, vp], i32),
+            "cdc_size_histogram": ([vp, sz, ctypes.c_uint64, ctypes.c_uint32, vp, vp], i32),
             "cdc_feed_create": ([ctypes.POINTER(vp), vp, i32, P], i32),
             "cdc_feed_push": ([vp, vp, sz, i32, vp, ctypes.POINTER(sz), vp], i32),
             "cdc_feed_position": ([vp, ctypes.POINTER(u64), ctypes.POINTER(u64)], i32),
@@ -117,7 +118,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return ["cdc_create", "cdc_destroy", "cdc_chunk", "cdc_chunk_async", "cdc_chunk_batch", "cdc_chunk_host",
             "cdc_reserve", "cdc_sync_status", "cdc_set_option", "cdc_get_option", "cdc_last_timing",
-            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_ebs", "cdc_rs", "cdc_fingerprint", "cdc_byte_shares", "cdc_feed_create", "cdc_feed_push",
+            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_ebs", "cdc_rs", "cdc_fingerprint", "cdc_byte_shares",
+            "cdc_size_histogram", "cdc_feed_create", "cdc_feed_push",
             "cdc_feed_position", "cdc_feed_reset", "cdc_feed_destroy", "cdc_server_create", "cdc_server_submit",
             "cdc_server_poll", "cdc_server_clock", "cdc_server_destroy", "cdc_status_string"]
 
@@ -465,6 +467,21 @@ def byte_shares(data, bounds, alg, w: int, mn: int, mx: int, stream=None):
     return v[0], v[1]
 
 
+def size_histogram(bounds, bin_width: int, n_bins: int, stream=None):
+    """Chunk-size histogram of a boundary list (int64 CUDA tensor, as chunk
+    returns): counts of sizes in [k * bin_width, (k + 1) * bin_width) for
+    k < n_bins - 1, the last bin taking every larger size (cdc_size_histogram).
+    Returns an int64 CUDA tensor of n_bins counts; its cumulative sum over the
+    chunk count is the chunk-size CDF."""
+    import torch
+    lib = load_library()
+    assert bounds.dtype == torch.int64 and bounds.is_cuda and bounds.is_contiguous()
+    h = torch.empty(n_bins, dtype=torch.int64, device=bounds.device)
+    _check(lib.cdc_size_histogram(bounds.data_ptr() if bounds.numel() else None, bounds.numel(), int(bin_width),
+                                  int(n_bins), h.data_ptr(), _stream_handle(stream)), "cdc_size_histogram")
+    return h
+
+
 def dedup_report(pieces):
     """Deduplication over a list of (uint8 CUDA tensor, its boundaries):
     chunks are equal when length and fingerprint are (Section 2.2, Eq. 1:
@@ -499,18 +516,21 @@ STATIC_MAX_LEN = 16 << 20
 
 def chunk_static(data, alg, w: int, mn: int, mx: int, out=None, stream=None):
     """cdc_chunk_static: boundaries of a uint8 CUDA tensor (at most
-    STATIC_MAX_LEN bytes) on the current device, with the library's fixed
+    STATIC_MAX_LEN bytes) on the tensor's device, with the library's fixed
     scratch and no handle. The library allocates nothing; `out` (int64 CUDA
-    tensor) is allocated here when not given. Calls must not overlap."""
+    tensor on the same device) is allocated here when not given. Calls must
+    not overlap."""
     import torch
     assert data.dtype == torch.uint8 and data.is_cuda and data.is_contiguous()
     lib = load_library()
     n = data.numel()
     if out is None:
         out = torch.empty(max_boundaries(n, mn), dtype=torch.int64, device=data.device)
+    assert out.dtype == torch.int64 and out.is_contiguous() and out.device == data.device
     cap = ctypes.c_size_t(out.numel())
-    st = lib.cdc_chunk_static(alg_id(alg), Params(w, mn, mx), data.data_ptr() if n else None, n, out.data_ptr(),
-                              ctypes.byref(cap), _stream_handle(stream))
+    with torch.cuda.device(data.device):
+        st = lib.cdc_chunk_static(alg_id(alg), Params(w, mn, mx), data.data_ptr() if n else None, n,
+                                  out.data_ptr(), ctypes.byref(cap), _stream_handle(stream))
     _check(st, "cdc_chunk_static (count %d)" % cap.value)
     return out[:cap.value]
 

@@ -259,8 +259,74 @@ __global__ void k_fingerprint(const uint8_t* base, uint64_t lo, const uint64_t* 
 // Targets come 32 bytes at a time: a warp max-scan of (byte + 1) gives the
 // maximum before each lane, carried across rounds. Totals go to out[0..1]
 // with one atomic per warp.
+// the maximum byte of data[a, b) (b > a) and the last position holding it, for
+// every lane of the warp
+__device__ __forceinline__ uint32_t warp_max_last(const uint8_t* data, uint64_t a, uint64_t b, uint64_t& at) {
+    const int lane = threadIdx.x & 31;
+    uint32_t best = 0;
+    uint64_t pos = a;
+    for (uint64_t i = a + (uint64_t)lane; i < b; i += 32) {
+        const uint32_t v = data[i];
+        if (v >= best) {
+            best = v;
+            pos = i;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t ob = __shfl_xor_sync(FULLMASK, best, o);
+        const uint64_t op = __shfl_xor_sync(FULLMASK, pos, o);
+        if (ob > best || (ob == best && op > pos)) {
+            best = ob;
+            pos = op;
+        }
+    }
+    at = pos;
+    return best;
+}
+
+// the first position in [a, b) whose byte is greater than t, or b
+__device__ __forceinline__ uint64_t warp_first_gt(const uint8_t* data, uint64_t a, uint64_t b, uint32_t t) {
+    const int lane = threadIdx.x & 31;
+    for (uint64_t b0 = a; b0 < b; b0 += 32) {
+        const uint64_t i = b0 + (uint64_t)lane;
+        const unsigned hit = __ballot_sync(FULLMASK, i < b && data[i] > t);
+        if (hit) return b0 + (uint64_t)(__ffs(hit) - 1);
+    }
+    return b;
+}
+
+// MAXP shares of the chunk from s, the procedure of Section 3.3 run by the
+// whole warp: GT scans for a byte above the maximum of its left window (that
+// maximum's last position m bounds the scan at m + w, where m leaves the
+// window), then a search of the right window of each byte the scan stops at
+__device__ void maxp_chunk_shares(const uint8_t* data, uint64_t len, uint64_t s, uint32_t w, uint32_t mn,
+                                  uint32_t mx, unsigned long long& ebs, unsigned long long& rs) {
+    const uint64_t L = len - s < mx ? len : s + mx;
+    const uint64_t cend = len > w ? (L < len - w ? L : len - w) : 0;
+    uint64_t p = s + mn - 1 > w ? s + mn - 1 : w;
+    while (p < cend) {
+        uint64_t m;
+        const uint32_t lmax = warp_max_last(data, p - w, p, m);
+        ebs += w;
+        const uint64_t stop = m + w + 1 < cend ? m + w + 1 : cend;
+        const uint64_t q = warp_first_gt(data, p, stop, lmax);
+        if (q >= stop) {
+            rs += stop - p;
+            p = stop;
+            continue;
+        }
+        rs += q - p + 1;
+        uint64_t at;
+        const uint32_t rmax = warp_max_last(data, q + 1, q + w + 1, at);
+        ebs += w;
+        if (data[q] > rmax) break;
+        p = q + 1;
+    }
+}
+
 __global__ void k_byte_shares(int alg, const uint8_t* data, uint64_t len, const uint64_t* bounds, uint64_t n,
-                              uint32_t w, uint32_t mn, unsigned long long* out) {
+                              uint32_t w, uint32_t mn, uint32_t mx, unsigned long long* out) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -269,6 +335,15 @@ __global__ void k_byte_shares(int alg, const uint8_t* data, uint64_t len, const 
     for (uint64_t c = warp; c < n; c += nwarps) {
         const uint64_t s = c ? bounds[c - 1] : 0, e = bounds[c];
         if (e <= s || e > len) continue;
+        if (alg == CDC_MAXP) {
+            unsigned long long ce = 0, cr = 0;
+            maxp_chunk_shares(data, len, s, w, mn, mx, ce, cr);
+            if (lane == 0) {
+                ebs += ce;
+                rs += cr;
+            }
+            continue;
+        }
         if (alg == CDC_RAM) {
             if (lane == 0) {
                 if (len - s <= w) {
@@ -321,17 +396,50 @@ __global__ void k_byte_shares(int alg, const uint8_t* data, uint64_t len, const 
     }
 }
 
+// chunk sizes b[i] - b[i-1] (b[-1] = 0) counted in n_bins bins of bin_width
+// bytes, the last bin taking every larger size; per-block counts in shared
+// memory, then one atomic per bin and block
+__global__ void k_size_hist(const uint64_t* bounds, uint64_t n, uint64_t bin_width, uint32_t n_bins,
+                            unsigned long long* hist) {
+    extern __shared__ unsigned int sh[];
+    for (uint32_t i = threadIdx.x; i < n_bins; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < n; c += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = c ? bounds[c - 1] : 0, e = bounds[c];
+        const uint64_t size = e > s ? e - s : 0;
+        const uint64_t b = size / bin_width;
+        atomicAdd(&sh[b < n_bins ? (uint32_t)b : n_bins - 1], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n_bins; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], (unsigned long long)sh[i]);
+}
+
 }  // namespace
 }  // namespace cdc
+
+extern "C" cdc_status cdc_size_histogram(const uint64_t* d_bounds, size_t n, uint64_t bin_width, uint32_t n_bins,
+                                         uint64_t* d_hist, cdc_stream stream) {
+    if (!d_hist || (n && !d_bounds) || bin_width == 0 || n_bins == 0 || n_bins > 8192) return CDC_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(d_hist, 0, n_bins * sizeof(uint64_t), st) != cudaSuccess) return CDC_ERR_CUDA;
+    if (n == 0) return CDC_OK;
+    uint64_t grid = (n + 255) / 256;
+    if (grid > 1024) grid = 1024;
+    cdc::k_size_hist<<<(unsigned)grid, 256, n_bins * sizeof(unsigned int), st>>>(
+        d_bounds, n, bin_width, n_bins, reinterpret_cast<unsigned long long*>(d_hist));
+    return cudaGetLastError() == cudaSuccess ? CDC_OK : CDC_ERR_CUDA;
+}
 
 extern "C" cdc_status cdc_byte_shares(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
                                       const uint64_t* d_bounds, size_t n, uint64_t* d_out, cdc_stream stream) {
     if ((int)alg < 0 || (int)alg > 3 || !d_out || (n && !d_bounds) || (len && !data)) return CDC_ERR_INVALID;
-    if (alg == CDC_MAXP || ((alg == CDC_AE || alg == CDC_AE_MIN) && p.min > p.w + 1)) return CDC_ERR_INVALID;
+    if (p.w < 1 || p.min < 1 || p.min > p.max) return CDC_ERR_INVALID;
+    if ((alg == CDC_AE || alg == CDC_AE_MIN) && p.min > p.w + 1) return CDC_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(d_out, 0, 2 * sizeof(uint64_t), st) != cudaSuccess) return CDC_ERR_CUDA;
     if (n == 0) return CDC_OK;
-    cdc::k_byte_shares<<<cdc::grid_for(n), 256, 0, st>>>((int)alg, data, len, d_bounds, n, p.w, p.min,
+    cdc::k_byte_shares<<<cdc::grid_for(n), 256, 0, st>>>((int)alg, data, len, d_bounds, n, p.w, p.min, p.max,
                                                           reinterpret_cast<unsigned long long*>(d_out));
     return cudaGetLastError() == cudaSuccess ? CDC_OK : CDC_ERR_CUDA;
 }

@@ -66,15 +66,57 @@ def test_empty_inputs():
 @pytest.mark.parametrize("offset", [0, 3])
 def test_byte_shares_match_oracle(offset):
     """cdc_byte_shares over the GPU's boundaries equals the oracle's search /
-    scan loop exactly (RAM, AE-Max, AE-Min; several windows)."""
+    scan loop exactly (RAM, AE-Max, AE-Min, MAXP; several windows; mixed,
+    uniform and low-alphabet bytes)."""
     import paper_2508_05797_gb300 as pkg
     from paper_2508_05797_gb300.cdc import CdcError, ERR_INVALID
-    data = synth.mixed_range(12, 64 << 20, 7 << 20, 6 << 20)
-    d = to_device(data, offset)
-    for alg, w, mn, mx in (("ram", 7936, 2048, 65536), ("ram", 100, 500, 3000), ("ae", 7000, 2048, 65536),
-                           ("ae", 64, 32, 700), ("ae_min", 3000, 1024, 20000)):
-        b = pkg.chunk(d, alg, w, mn, mx)
-        assert pkg.byte_shares(d, b, alg, w, mn, mx) == oracle.byte_shares(alg, data, w, mn, mx), (alg, w)
+    rng = np.random.default_rng(offset)
+    for data in (synth.mixed_range(12, 64 << 20, 7 << 20, 6 << 20), synth.uniform(13, (1 << 20) + 77),
+                 rng.integers(0, 3, size=300_001).astype(np.uint8)):
+        d = to_device(data, offset)
+        for alg, w, mn, mx in (("ram", 7936, 2048, 65536), ("ram", 100, 500, 3000), ("ae", 7000, 2048, 65536),
+                               ("ae", 64, 32, 700), ("ae_min", 3000, 1024, 20000), ("maxp", 291, 2048, 65536),
+                               ("maxp", 63, 1, 3000), ("maxp", 7, 40, 300), ("maxp", 1000, 1, 5000)):
+            b = pkg.chunk(d, alg, w, mn, mx)
+            assert pkg.byte_shares(d, b, alg, w, mn, mx) == oracle.byte_shares(alg, data, w, mn, mx), (alg, w)
     with pytest.raises(CdcError) as ei:
-        pkg.byte_shares(d, pkg.chunk(d, "maxp", 300, 2048, 65536), "maxp", 300, 2048, 65536)
+        pkg.byte_shares(d, pkg.chunk(d, "ae", 300, 200, 65536), "ae", 300, 400, 65536)
     assert ei.value.status == ERR_INVALID
+
+
+def _host_hist(bounds, width, n_bins):
+    sizes = np.diff(np.concatenate([[0], np.asarray(bounds, dtype=np.int64)]))
+    return np.bincount(np.minimum(sizes // width, n_bins - 1), minlength=n_bins)
+
+
+def test_size_histogram_equals_oracle_sizes():
+    """The device chunk-size histogram of each algorithm's boundaries equals
+    the histogram of the oracle's chunk sizes counted on the host (the size
+    CDF is its running sum over the chunk count)."""
+    import torch
+    import paper_2508_05797_gb300 as pkg
+    from gpu_util import params
+    data = synth.mixed_range(1, 4 << 30, 0, 24 << 20)
+    d = torch.from_numpy(data).cuda()
+    for alg in ("ram", "ae", "ae_min", "maxp"):
+        w, mn, mx = params("mixed_4g_seed1", "ae" if alg == "ae_min" else alg, 8192)
+        exp = oracle.chunk(alg, data, w, mn, mx)
+        b = pkg.chunk(d, alg, w, mn, mx)
+        for width, n_bins in ((1024, 64), (4096, 17), (1, 8192), (1 << 20, 3)):
+            h = pkg.size_histogram(b, width, n_bins).cpu().numpy()
+            assert np.array_equal(h, _host_hist(exp, width, n_bins)), (alg, width, n_bins)
+
+
+def test_size_histogram_edges():
+    import torch
+    import paper_2508_05797_gb300 as pkg
+    from paper_2508_05797_gb300.cdc import CdcError, ERR_INVALID
+    empty = torch.zeros(0, dtype=torch.int64, device="cuda")
+    assert pkg.size_histogram(empty, 100, 5).cpu().tolist() == [0] * 5
+    b = torch.tensor([1, 1, 101, 5000, 5000 + (1 << 40)], dtype=torch.int64, device="cuda")
+    assert pkg.size_histogram(b, 100, 4).cpu().tolist() == [2, 1, 0, 2]
+    assert pkg.size_histogram(b, 1 << 50, 1).cpu().tolist() == [5]
+    for width, n_bins in ((0, 4), (100, 0), (100, 8193)):
+        with pytest.raises(CdcError) as ei:
+            pkg.size_histogram(b, width, n_bins)
+        assert ei.value.status == ERR_INVALID
