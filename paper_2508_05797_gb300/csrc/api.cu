@@ -1073,6 +1073,16 @@ static cdc_status fixed_scratch(int dev, cudaStream_t st, uint8_t** out) {
     return CDC_OK;
 }
 
+// true when p is memory of device `dev` or managed memory
+static bool device_memory_of(const void* p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
+}
+
 extern "C" cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t* data, size_t len,
                                        uint64_t* out_bounds, size_t* n, cdc_stream stream) {
     if (!n || !valid_params(alg, p)) return CDC_ERR_INVALID;
@@ -1084,6 +1094,7 @@ extern "C" cdc_status cdc_chunk_static(cdc_alg alg, cdc_params p, const uint8_t*
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CDC_ERR_CUDA;
+    if (!device_memory_of(data, dev) || !device_memory_of(out_bounds, dev)) return CDC_ERR_INVALID;
     uint8_t* scr = nullptr;
     cdc_status s = fixed_scratch(dev, st, &scr);
     if (s != CDC_OK) return s;

@@ -117,3 +117,28 @@ def test_no_device_memory_is_taken(env):
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0
+
+
+def test_host_memory_is_refused(env):
+    """Pointers that are not the current device's memory return INVALID
+    before anything is enqueued (the output keeps its contents)."""
+    torch, pkg, lib, ck = env
+    w, mn, mx = 300, 64, 4096
+    host_np = synth.uniform(4, 1 << 16)
+    pinned = torch.from_numpy(host_np).pin_memory()
+    data = to_device(host_np)
+    out = torch.full((pkg.max_boundaries(data.numel(), mn),), -1, dtype=torch.int64, device="cuda")
+    out_pinned = torch.full(out.shape, -1, dtype=torch.int64).pin_memory()
+    out_np = np.full(out.numel(), -1, dtype=np.int64)
+    stream = torch.cuda.current_stream().cuda_stream
+    for src, dst in ((pinned.data_ptr(), out.data_ptr()), (host_np.ctypes.data, out.data_ptr()),
+                     (data.data_ptr(), out_pinned.data_ptr()), (data.data_ptr(), out_np.ctypes.data)):
+        n = ctypes.c_size_t(out.numel())
+        st = lib.cdc_chunk_static(0, pkg.Params(w, mn, mx), src, host_np.size, dst, ctypes.byref(n), stream)
+        assert st == INVALID
+    torch.cuda.synchronize()
+    assert int(out.max()) == -1 and int(out_pinned.max()) == -1 and int(out_np.max()) == -1
+    # the Python wrapper refuses an output on another device than the data
+    with pytest.raises(AssertionError):
+        pkg.chunk_static(data, "ram", w, mn, mx, out=torch.empty(out.numel(), dtype=torch.int64))
+    assert torch.equal(pkg.chunk_static(data, "ram", w, mn, mx), ck.chunk(data, "ram", w, mn, mx))
