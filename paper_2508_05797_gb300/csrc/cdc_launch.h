@@ -179,7 +179,12 @@ enum : int {
     GST_CC_LIST = 11,      //   listing the blocks that can hold a candidate
     GST_CC_BLOCKS = 12,    //   testing the listed blocks' bytes
     GST_CC_WRITE = 13,     //   writing the candidates
-    GST_CC_LISTED = 14     // blocks listed
+    GST_CC_LISTED = 14,    // blocks listed
+    GST_MAX_STAGE = 15,    // local kernel, the longest segment of each phase (cycles): staging
+    GST_MAX_F = 16,        //   F
+    GST_MAX_JUMP = 17,     //   pointer jumping
+    GST_MAX_SEG_AT = 18,   // (cycles << 24) | segment of the longest local segment
+    GST_CC_MAX = 19        // candidate kernel: the longest chunk (cycles)
 };
 
 struct GraphGrids {

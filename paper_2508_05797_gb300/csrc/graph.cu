@@ -34,6 +34,7 @@
 #include "cdc_device.cuh"
 #include "cdc_launch.h"
 #include "graph_logic.cuh"
+#include "warp_rules.cuh"
 
 namespace cdc {
 
@@ -41,6 +42,7 @@ constexpr int GC_THREADS = 256;  // k_gcand
 constexpr int GL_THREADS = 512;  // k_gjump
 constexpr int GL_PER = 8;        // candidates per thread in the jumping rounds
 constexpr uint32_t GL_EXIT = 0xFFFFFFFFu;
+constexpr uint32_t GL_PEND = 0xFFFFFFFEu;  // F not yet known (k_glocal)
 constexpr int GE_BUF = 256;      // k_gemit: boundaries buffered before a store
 
 __device__ __forceinline__ uint64_t g_seg_lo(const GraphLaunch& A, uint32_t k) { return A.lo + (uint64_t)k * A.S; }
@@ -410,6 +412,7 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
                 atomicAdd(&A.stats[GST_CC_BLOCKS], (unsigned long long)(c3 - c2));
                 atomicAdd(&A.stats[GST_CC_WRITE], (unsigned long long)(c4 - c3));
                 atomicAdd(&A.stats[GST_CC_LISTED], (unsigned long long)nl);
+                atomicMax(&A.stats[GST_CC_MAX], (unsigned long long)(c4 - c0));
             }
         }
         if (tid == 0) A.cnum[seg] = run;
@@ -431,9 +434,149 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
 // shared memory of k_glocal: lists of 2 cap entries (positions, bytes), three
 // jumping arrays of cap words, and the staged block maxima with their running
 // maxima inside superblocks (`win` bytes each)
-__host__ __device__ inline uint32_t gl_stage_off(uint32_t cap) { return (22u * cap + 15u) & ~15u; }
+__host__ __device__ inline uint32_t gl_stage_off(uint32_t cap) { return (22u * cap + cap / 16u + 15u) & ~15u; }
+// (the queue of candidates whose F steps the chain, one word per candidate, follows)
+__host__ __device__ inline uint32_t gl_queue_off(int rule, uint32_t cap, uint32_t win) {
+    return gl_stage_off(cap) + (rule == RULE_MAXP ? 0u : 3u * win);
+}
 int graph_local_smem(int rule, uint32_t cap, uint32_t win) {
-    return (int)gl_stage_off(cap) + (rule == RULE_MAXP ? 0 : 3 * (int)win);
+    return (int)(gl_queue_off(rule, cap, win) + 4u * cap);
+}
+
+// Is position y a candidate (is_cand), decided by the whole warp
+template <int RULE>
+__device__ bool w_is_cand(const SumView& S, const RawView& R, const Prm& P, uint64_t lo, uint64_t hi, uint64_t y) {
+    uint64_t a, b;
+    cand_source_range<RULE>(P, lo, hi, &a, &b);
+    const uint64_t sh = cand_shift<RULE>(P);
+    if (y < sh) return false;
+    const uint64_t q = y - sh;
+    if (q < a || q >= b) return false;
+    if (RULE == RULE_MAXP) return S.m(q >> 6) == (uint32_t)(q & 63);
+    const uint32_t x = R.byte(q);
+    if (x == 0) return false;
+    if (x == 255) return true;
+    if (RULE == RULE_RAM) return w_range_max(S, R, q - P.w, q) <= x;
+    return w_range_max(S, R, q + 1, q + P.w + 1) <= x;
+}
+
+// Range Scan (GEQ) over [from, to) for the whole warp: whole 4 KiB superblocks
+// whose maximum is below M are skipped 32 at a time (a ballot over their
+// summaries), the rest as w_first_geq. Equals first_geq.
+__device__ uint64_t w_first_geq_far(const SumView& S, const RawView& R, uint64_t from, uint64_t to, uint32_t M,
+                                    uint32_t* val) {
+    uint64_t p = from;
+    while (p < to) {
+        if ((p & 4095) == 0 && S.sup && p + 4096 <= to) {
+            const uint64_t q0 = p >> 12, qn = (to >> 12) - q0;  // whole superblocks before `to`
+            const bool hit = (uint64_t)lane_id() < qn && S.sup[q0 + lane_id()] >= M;
+            const uint32_t bal = __ballot_sync(FULL, hit);
+            if (bal == 0) {
+                p = (q0 + umin64(qn, 32)) << 12;
+                continue;
+            }
+            const int l = __ffs((int)bal) - 1;
+            if (l > 0) {
+                p = (q0 + (uint64_t)l) << 12;
+                continue;
+            }
+        }
+        const uint64_t e = umin64(to, ((p >> 12) + 1) << 12);  // to the end of p's superblock
+        const uint64_t r = w_first_geq(S, R, p, e, M, val);
+        if (r < e) return r;
+        p = e;
+    }
+    return to;
+}
+
+// RAM next(s) for the whole warp, the scan skipping superblocks (equals next_ram)
+__device__ uint64_t w_next_ram_far(const SumView& S, const RawView& R, const Prm& P, uint64_t fhi, uint64_t s) {
+    if (fhi - s <= P.w) return fhi;
+    const uint64_t limit = umin64(fhi, s + P.mx);
+    const uint64_t t = s + P.w;
+    const uint32_t M = w_range_max(S, R, s, t);
+    const uint64_t j0 = umax64(t, s + P.mn - 1);
+    if (j0 >= limit) return limit;
+    if (M == 0) return j0 + 1;
+    uint32_t val;
+    const uint64_t j = w_first_geq_far(S, R, j0, limit, M, &val);
+    return j < limit ? j + 1 : limit;
+}
+
+// advance_far() for the whole warp: k steps of stride d, then e (quiet runs and
+// runs of forced cuts in one call), the RAM scan skipping superblocks
+template <int RULE>
+__device__ uint64_t w_advance_far(const SumView& S, const RawView& R, const Prm& P, uint64_t flo, uint64_t fhi,
+                                  uint64_t s, uint64_t stop, uint32_t* k, uint64_t* d) {
+    if (RULE == RULE_RAM) {
+        const uint64_t w = P.w, st = w + 1;
+        if (P.mn <= st && s + w < fhi && S.m(s >> 6) == 0 && S.m((s + w - 1) >> 6) == 0) {
+            const uint64_t kstop = (stop - 1 - s) / st + 1;
+            const uint64_t kfhi = (fhi - 1 - s - w) / st + 1;
+            const uint64_t kmax = kstop < kfhi ? kstop : kfhi;
+            const uint64_t z = w_first_nonzero(S, R, s, s + (kmax - 1) * st + w + 1);
+            const uint64_t kz = z > s + w ? (z - 1 - s - w) / st + 1 : 0;
+            const uint64_t kk = kz < kmax ? kz : kmax;
+            if (kk >= 2) {
+                *k = (uint32_t)kk;
+                *d = st;
+                return s + kk * st;
+            }
+        }
+        const uint64_t e = w_next_ram_far(S, R, P, fhi, s);
+        *k = 1;
+        *d = e - s;
+        return e;
+    }
+    return w_advance<RULE>(S, R, P, flo, fhi, s, stop, k, d);
+}
+
+// F(y) by stepping the chain (cand_next_t) with every step shared by the
+// warp's lanes (warp_rules.cuh): the same landing and count. Quiet runs and
+// runs of forced cuts are crossed in one step; their cuts are not candidates.
+template <int RULE>
+__device__ uint64_t w_cand_next(const SumView& S, const RawView& R, const Prm& P, uint64_t lo, uint64_t hi,
+                                uint64_t y, uint32_t* n) {
+    uint64_t s = y;
+    uint32_t c = 0;
+    for (;;) {
+        uint64_t e;
+        if (RULE == RULE_RAM || RULE == RULE_AE) {
+            const uint64_t w = P.w, st = w + 1;
+            if (P.mn <= st && s + w < hi && S.m(s >> 6) == 0 && S.m((s + w - 1) >> 6) == 0) {
+                // a zero run: cuts every w + 1 bytes, none of them a candidate
+                const uint64_t kmax = (hi - 1 - s - w) / st + 1;
+                const uint64_t z = w_first_nonzero(S, R, s, s + (kmax - 1) * st + w + 1);
+                const uint64_t kz = z > s + w ? (z - 1 - s - w) / st + 1 : 0;
+                const uint64_t kk = kz < kmax ? kz : kmax;
+                if (kk >= 1) {
+                    c += (uint32_t)kk;
+                    s += kk * st;
+                    if (s >= hi) {
+                        *n = c;
+                        return hi;
+                    }
+                    continue;
+                }
+            }
+            e = RULE == RULE_RAM ? w_next_ram_far(S, R, P, hi, s) : w_next_ae(S, R, P, hi, s);
+            c++;
+        } else {
+            uint32_t k;
+            uint64_t d;
+            e = w_advance<RULE>(S, R, P, lo, hi, s, hi, &k, &d);
+            c += k;
+        }
+        if (e >= hi || e <= s) {  // (e <= s cannot happen: every chunk holds a byte)
+            *n = c;
+            return hi;
+        }
+        if (w_is_cand<RULE>(S, R, P, lo, hi, e)) {
+            *n = c;
+            return e;
+        }
+        s = e;
+    }
 }
 
 // window maximum over bytes [a, b): blocks [sb0, sb0 + sn) staged (sm) with
@@ -517,10 +660,12 @@ __global__ void __launch_bounds__(GL_THREADS, 1) k_glocal(GraphLaunch A) {
     uint32_t* C = J + cap;                                // chunk ends covered by the jump
     uint32_t* X = C + cap;                                // exit id (valid once J is GL_EXIT)
     uint8_t* lval = reinterpret_cast<uint8_t*>(X + cap);  // the candidates' bytes
+    uint8_t* lgm = lval + 2 * cap;                        // their maxima per group of 32
     uint8_t* sm = smem + gl_stage_off(cap);               // staged block maxima
     uint8_t* spr = sm + A.win;                            // running maxima inside superblocks (staged)
     uint8_t* ssf = sm + 2 * A.win;
-    __shared__ uint32_t s_seg;
+    uint32_t* pq = reinterpret_cast<uint32_t*>(smem + gl_queue_off(RULE, cap, A.win));  // F by stepping
+    __shared__ uint32_t s_seg, s_np;
     const int tid = threadIdx.x;
     const Prm P{A.w, A.mn, A.mx};
     const RawView R{A.base, A.inv};
@@ -530,7 +675,10 @@ __global__ void __launch_bounds__(GL_THREADS, 1) k_glocal(GraphLaunch A) {
     unsigned long long* st = A.stats;  // counters (testing only)
     for (;;) {
         long long t0 = st ? clock64() : 0;
-        if (tid == 0) s_seg = (uint32_t)atomicAdd(A.ticket, 1ull);
+        if (tid == 0) {
+            s_seg = (uint32_t)atomicAdd(A.ticket, 1ull);
+            s_np = 0;
+        }
         __syncthreads();
         const uint32_t seg = s_seg;
         if (seg >= A.nseg) break;
@@ -582,22 +730,49 @@ __global__ void __launch_bounds__(GL_THREADS, 1) k_glocal(GraphLaunch A) {
         }
         __syncthreads();
         long long t1 = st ? clock64() : 0;
+        for (uint32_t g = tid; g < (n + nla + 31) / 32; g += GL_THREADS) {
+            uint32_t m = 0;
+            for (uint32_t i = g * 32; i < g * 32 + 32 && i < n + nla; i++) m = lval[i] > m ? lval[i] : m;
+            lgm[g] = (uint8_t)m;
+        }
+        __syncthreads();
         const WMaxStaged wm{sm, A.spre ? spr : nullptr, ssf, sb0, sn, &S, &T, &R};
-        const CandList L{lpos, lval, n + nla, a, cover};
+        const CandList L{lpos, lval, n + nla, a, cover, lgm};
+        // F from the lists; the candidates the lists cannot decide are queued
         for (uint32_t i = tid; i < n; i += GL_THREADS) {
             const uint64_t y = a + lpos[i];
-            uint32_t c = 1, ft, jj = GL_EXIT;
-            const uint32_t k = list_next<RULE>(L, wm, R, P, A.lo, A.hi, y);
-            if (k != LIST_GENERIC) {
-                if (k < n) {
-                    ft = seg * cap + k;
-                    jj = k;
-                } else {
-                    ft = (seg + 1) * cap + (k - n);
-                }
+            uint32_t cnt;
+            const uint32_t k = list_next<RULE>(L, wm, R, P, A.lo, A.hi, y, &cnt);
+            if (k == LIST_GENERIC) {
+                J[i] = GL_PEND;
+                pq[atomicAdd(&s_np, 1u)] = i;
+                continue;
+            }
+            uint32_t ft, jj = GL_EXIT;
+            if (k < n) {
+                ft = seg * cap + k;
+                jj = k;
             } else {
+                ft = (seg + 1) * cap + (k - n);
+            }
+            A.cft[base + i] = ft;
+            A.csc[base + i] = cnt;
+            J[i] = jj;
+            C[i] = cnt;
+            X[i] = ft;
+        }
+        __syncthreads();
+        {
+            // the queued candidates, one warp each: F by stepping the chain
+            const uint32_t np = s_np;
+            const int lane = tid & 31;
+            for (uint32_t q = (uint32_t)(tid >> 5); q < np; q += GL_THREADS / 32) {
+                const uint32_t i = pq[q];
+                const uint64_t y = a + lpos[i];
+                uint32_t c = 1, ft, jj = GL_EXIT;
                 const long long tg = st ? clock64() : 0;
-                const uint64_t e = cand_next_t<RULE>(S, T, R, P, A.lo, A.hi, y, &c);
+                const uint64_t e = w_cand_next<RULE>(S, R, P, A.lo, A.hi, y, &c);
+                if (lane != 0) continue;
                 if (st) {
                     const unsigned long long dt = (unsigned long long)(clock64() - tg);
                     atomicAdd(&st[GST_GENERIC], 1ull);
@@ -630,12 +805,12 @@ __global__ void __launch_bounds__(GL_THREADS, 1) k_glocal(GraphLaunch A) {
                         }
                     }
                 }
+                A.cft[base + i] = ft;
+                A.csc[base + i] = c;
+                J[i] = jj;
+                C[i] = c;
+                X[i] = ft;
             }
-            A.cft[base + i] = ft;
-            A.csc[base + i] = c;
-            J[i] = jj;
-            C[i] = c;
-            X[i] = ft;
         }
         __syncthreads();
         long long t2 = st ? clock64() : 0;
@@ -679,6 +854,10 @@ __global__ void __launch_bounds__(GL_THREADS, 1) k_glocal(GraphLaunch A) {
             atomicAdd(&st[GST_CYC_JUMP], (unsigned long long)(t3 - t2));
             atomicAdd(&st[GST_ROUNDS], (unsigned long long)rounds);
             atomicMax(&st[GST_MAX_SEG], (unsigned long long)(t3 - t0));
+            atomicMax(&st[GST_MAX_STAGE], (unsigned long long)(t1 - t0));
+            atomicMax(&st[GST_MAX_F], (unsigned long long)(t2 - t1));
+            atomicMax(&st[GST_MAX_JUMP], (unsigned long long)(t3 - t2));
+            atomicMax(&st[GST_MAX_SEG_AT], ((unsigned long long)(t3 - t0) << 24) | seg);
         }
         __syncthreads();  // shared arrays (and s_seg) are reused by the next segment
     }
@@ -842,7 +1021,8 @@ __global__ void __launch_bounds__(GE_THREADS) k_gemit(GraphLaunch A) {
         uint64_t y = a + spos[id0 - base];
         uint32_t cur = id0 - (uint32_t)base;
         for (;;) {
-            if (tid == 0) {
+            if (tid < 32) {  // warp 0 walks (every lane the same state); lane 0 fills the buffer
+                const int lane = tid;
                 uint32_t held = 0;
                 unsigned long long nb = s_nb;  // boundaries stored so far
                 bool done = false;
@@ -854,7 +1034,8 @@ __global__ void __launch_bounds__(GE_THREADS) k_gemit(GraphLaunch A) {
                         if (ft == GID_END) e = A.hi;
                         else if (ft >= (uint32_t)base && ft - (uint32_t)base < n) e = a + spos[ft - (uint32_t)base];
                         else e = g_pos(A, ft);
-                        buf[held++] = e - A.lo;
+                        if (lane == 0) buf[held] = e - A.lo;
+                        held++;
                         nxt = ft;
                     } else {
                         // step the chain: every end up to the next candidate
@@ -862,19 +1043,27 @@ __global__ void __launch_bounds__(GE_THREADS) k_gemit(GraphLaunch A) {
                         for (;;) {
                             uint32_t k;
                             uint64_t d;
-                            const uint64_t e2 = advance_far<RULE>(S, R, P, A.lo, A.hi, s2, A.hi, &k, &d);
+                            const uint64_t e2 = w_advance_far<RULE>(S, R, P, A.lo, A.hi, s2, A.hi, &k, &d);
                             for (uint32_t t = 1; t <= k; t++) {
-                                buf[held++] = s2 + t * d - A.lo;
+                                if (lane == 0) buf[held] = s2 + t * d - A.lo;
+                                held++;
                                 if (held == GE_BUF) {
-                                    // rare (long quiet or forced runs): store from this thread
-                                    for (uint32_t q = 0; q < held; q++)
+                                    // rare (long quiet or forced runs): the warp stores the buffer
+                                    __syncwarp();
+                                    for (uint32_t q = (uint32_t)lane; q < held; q += 32)
                                         if (off0 + nb + q < A.capacity) A.out[off0 + nb + q] = buf[q];
+                                    __syncwarp();
                                     nb += held;
                                     held = 0;
                                 }
                             }
+                            if (e2 <= s2) {  // (cannot happen: every chunk holds a byte)
+                                g_fail(A, seg);
+                                s2 = A.hi;
+                                break;
+                            }
                             s2 = e2;
-                            if (e2 >= A.hi || is_cand<RULE>(S, R, P, A.lo, A.hi, e2)) break;
+                            if (e2 >= A.hi || w_is_cand<RULE>(S, R, P, A.lo, A.hi, e2)) break;
                         }
                         e = s2;
                         if (ft != GID_SLOW) nxt = ft;
@@ -895,9 +1084,11 @@ __global__ void __launch_bounds__(GE_THREADS) k_gemit(GraphLaunch A) {
                                   : ~0u;
                     }
                 }
-                s_nb = nb;
-                s_held = held;
-                s_done = done ? 1 : 0;
+                if (lane == 0) {
+                    s_nb = nb;
+                    s_held = held;
+                    s_done = done ? 1 : 0;
+                }
             }
             __syncthreads();
             const uint32_t held = s_held;

@@ -599,7 +599,9 @@ CDC_HD uint64_t cand_next(const SumView& S, const RawView& R, const Prm& P, uint
 //   RAM : the cut byte is the first byte >= M (the window maximum) at or past
 //         s + w; that byte is itself a candidate, and every candidate before
 //         it in that range is below M -- the first listed candidate from
-//         s + w whose byte is >= M.
+//         s + w whose byte is >= M. With none before s + max the chunk is
+//         forced to end at s + max: F is that position if it is listed, else
+//         the list decides the next chunk from there the same way.
 //   AE  : the cut follows the first target (a strict prefix maximum from s)
 //         with no greater byte in its window -- the first listed candidate q
 //         >= s whose byte exceeds every byte of [s, q).
@@ -614,7 +616,25 @@ struct CandList {
     const uint8_t* val;
     uint32_t n;
     uint64_t base, cover;
+    const uint8_t* gmax;  // maximum of val[32 g .. 32 g + 31] per group g, or null
 };
+
+// first index >= k whose position is <= ymax and whose byte is >= M; L.n if none
+CDC_HD uint32_t list_first_geq(const CandList& L, uint32_t k, uint64_t ymax, uint32_t M) {
+    while (k < L.n) {
+        if (L.gmax && (k & 31) == 0 && L.gmax[k >> 5] < M) {
+            // the whole group is below M: skip it unless it reaches past ymax
+            const uint32_t last = k + 31 < L.n ? k + 31 : L.n - 1;
+            if (L.base + L.pos[last] > ymax) return L.n;
+            k += 32;
+            continue;
+        }
+        if (L.base + L.pos[k] > ymax) return L.n;
+        if (L.val[k] >= M) return k;
+        k++;
+    }
+    return L.n;
+}
 
 CDC_HD uint32_t list_lower_bound(const CandList& L, uint64_t y) {
     if (y <= L.base) return 0;
@@ -628,24 +648,39 @@ CDC_HD uint32_t list_lower_bound(const CandList& L, uint64_t y) {
     return lo;
 }
 
-// Index in L of F(s) when the chain's first step from s is a natural cut that
-// the list decides, else LIST_GENERIC. wmax(a, b) is the maximum byte of [a, b)
-// (a < b); R reads single bytes (AE's start byte).
+// Index in L of F(s) when the list decides the chain from s (natural cuts, and
+// for RAM forced cuts before one), else LIST_GENERIC; *cnt = the chunk ends up
+// to F. wmax(a, b) is the maximum byte of [a, b) (a < b); R reads single
+// bytes (AE's start byte).
 template <int RULE, class WMax>
 CDC_HD uint32_t list_next(const CandList& L, const WMax& wmax, const RawView& R, const Prm& P, uint64_t lo,
-                          uint64_t hi, uint64_t s) {
+                          uint64_t hi, uint64_t s, uint32_t* cnt) {
     const uint64_t w = P.w;
     const uint64_t limit = umin64(hi, s + P.mx);
+    *cnt = 1;
     if (RULE == RULE_RAM) {
-        if (hi - s <= w) return LIST_GENERIC;
-        const uint64_t j0 = s + w;  // min <= w + 1
-        if (j0 >= limit) return LIST_GENERIC;
-        const uint32_t M = wmax(s, j0);
-        if (M == 0) return LIST_GENERIC;
-        for (uint32_t k = list_lower_bound(L, j0 + 1); k < L.n; k++) {
-            const uint64_t y = L.base + L.pos[k];
-            if (y > limit || y > L.cover) return LIST_GENERIC;
-            if (L.val[k] >= M) return k;
+        uint64_t s0 = s;
+        for (uint32_t c = 1; c <= 4; c++) {
+            const uint64_t lim = umin64(hi, s0 + P.mx);
+            if (hi - s0 <= w) return LIST_GENERIC;
+            const uint64_t j0 = s0 + w;  // min <= w + 1
+            if (j0 >= lim) return LIST_GENERIC;
+            const uint32_t M = wmax(s0, j0);
+            if (M == 0) return LIST_GENERIC;
+            const uint64_t ymax = umin64(lim, L.cover);
+            const uint32_t k = list_first_geq(L, list_lower_bound(L, j0 + 1), ymax, M);
+            if (k < L.n) {
+                *cnt = c;
+                return k;
+            }
+            // no natural cut up to ymax: a forced cut at lim, if the list covers it
+            if (lim > L.cover || lim >= hi) return LIST_GENERIC;
+            const uint32_t kf = list_lower_bound(L, lim);
+            if (kf < L.n && L.base + L.pos[kf] == lim) {
+                *cnt = c;
+                return kf;
+            }
+            s0 = lim;
         }
         return LIST_GENERIC;
     }

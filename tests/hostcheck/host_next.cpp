@@ -1,6 +1,7 @@
 // Test-only host build of the chain stage's per-thread chunk rules
 // (paper_2508_05797_gb300/csrc/chain_logic.cuh), so that the summary-based
 // rules can be compared with the CPU oracle without a GPU.
+#include <vector>
 #include <stdint.h>
 #include <string.h>
 
@@ -215,19 +216,23 @@ extern "C" uint64_t hc_list_check(int rule, const uint8_t* base, const uint8_t* 
     RawView R{base, inv};
     Prm P{w, mn, mx};
     PreSuf T{nullptr, nullptr};
-    CandList L{pos, val, n, lbase, hi};
+    // group maxima of the list, as the local kernel builds them
+    std::vector<uint8_t> gm((n + 31) / 32, 0);
+    for (uint32_t i = 0; i < n; i++) gm[i / 32] = val[i] > gm[i / 32] ? val[i] : gm[i / 32];
+    CandList L{pos, val, n, lbase, hi, gm.data()};
     WMaxSum wm{&S, &T, &R};
     return with_rule(rule, [&](auto rc) -> uint64_t {
         constexpr int RU = decltype(rc)::value;
         uint64_t decided = 0;
         for (uint32_t i = 0; i < n; i++) {
             const uint64_t y = lbase + pos[i];
-            const uint32_t k = list_next<RU>(L, wm, R, P, lo, hi, y);
+            uint32_t lc = 0;
+            const uint32_t k = list_next<RU>(L, wm, R, P, lo, hi, y, &lc);
             out[i] = k;
             if (k == LIST_GENERIC) continue;
             uint32_t c = 0;
             const uint64_t e = cand_next<RU>(S, R, P, lo, hi, y, &c);
-            if (c != 1 || e != lbase + pos[k]) return ~0ull - i;
+            if (c != lc || e != lbase + pos[k]) return ~0ull - i;
             decided++;
         }
         return decided;

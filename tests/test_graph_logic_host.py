@@ -78,6 +78,10 @@ def _datasets(n, seed):
         "zero_runs": zeros,
         "ternary": rng.integers(0, 3, size=n).astype(np.uint8),
         "ramp": (np.arange(n) % 251).astype(np.uint8),
+        # random bytes, then text-like bytes: RAM chains from the random part
+        # meet forced cuts in the text before their next natural cut
+        "uniform_then_text": np.concatenate([synth.uniform(seed + 1, n // 2),
+                                             synth.mixed_range(1, 4 << 30, 6 << 20, n - n // 2)]),
     }
 
 
