@@ -266,25 +266,29 @@ void cdc_server_s::finish(Slot& s) {
 
 void cdc_server_s::run() {
     cudaSetDevice(device);
-    std::deque<Request> pending;
+    // `ready`: arrived requests in arrival order (what a batch is packed from);
+    // `future`: requests whose arrival time lies ahead, sorted by it. Batching
+    // scans only the arrived requests, however many are submitted ahead.
+    std::deque<Request> ready, future;
+    auto by_arrival = [](const Request& a, const Request& b) { return a.t_arrive < b.t_arrive; };
     for (;;) {
         {
             std::unique_lock<std::mutex> lock(mu);
             const bool any_busy = std::any_of(slots.begin(), slots.end(), [](const Slot& s) { return s.busy; });
-            if (inbox.empty() && !any_busy) {
-                if (pending.empty()) {
+            if (inbox.empty() && !any_busy && ready.empty()) {
+                if (future.empty()) {
                     if (stop) break;
                     cv.wait_for(lock, std::chrono::milliseconds(2));
                 } else {
                     // waiting only for arrival times: sleep until the next one (or new work)
-                    double next = pending.front().t_arrive;
-                    for (const Request& r : pending) next = std::min(next, r.t_arrive);
-                    const double d = next - now_ms();
+                    const double d = future.front().t_arrive - now_ms();
                     if (d > 0.05) cv.wait_for(lock, std::chrono::microseconds((int64_t)(d * 1000.0)));
                 }
             }
             while (!inbox.empty()) {
-                pending.push_back(inbox.front());
+                const Request& r = inbox.front();
+                if (future.empty() || !by_arrival(r, future.back())) future.push_back(r);  // the usual case
+                else future.insert(std::upper_bound(future.begin(), future.end(), r, by_arrival), r);
                 inbox.pop_front();
             }
         }
@@ -296,8 +300,12 @@ void cdc_server_s::run() {
             }
         }
         const double t = now_ms();
+        while (!future.empty() && future.front().t_arrive <= t) {
+            ready.push_back(future.front());
+            future.pop_front();
+        }
         for (Slot& s : slots)
-            if (!s.busy && !pending.empty() && launch(s, pending, t)) progress = true;
+            if (!s.busy && !ready.empty() && launch(s, ready, t)) progress = true;
         if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     for (Slot& s : slots)
