@@ -470,7 +470,7 @@ static bool use_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan& pl, u
 
 static cdc_status run_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan& pl, const Geo& g,
                             const GraphGeo& gg, uint64_t* out, uint64_t capacity, uint64_t* d_count,
-                            cudaStream_t st) {
+                            cudaStream_t st, uint64_t ctx) {
     (void)alg;
     cdc_status s;
     const size_t slots = (size_t)gg.nseg * gg.cap;
@@ -525,7 +525,8 @@ static cdc_status run_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan&
     GraphLaunch ga;
     memset(&ga, 0, sizeof ga);
     ga.base = g.base;
-    ga.lo = g.lo;
+    ga.flo = g.lo;  // the summaries cover the context bytes too
+    ga.lo = g.lo + ctx;
     ga.hi = g.hi;
     ga.smax = h->smax;
     ga.sarg = h->sarg ? h->sarg : h->smax;
@@ -592,7 +593,8 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     const uint64_t seg = pick_seg(h, alg, p, len, batch ? n_files : 1);
     const uint64_t items = batch ? len / seg + n_files + 1 : (len + seg - 1) / seg;
     GraphGeo gg;
-    const bool graph = !batch && ctx == 0 && use_graph(h, alg, p, pl, len, &gg);
+    // (a left context only exists for MAXP, whose targets may use it as window bytes)
+    const bool graph = !batch && (ctx == 0 || pl.rule == RULE_MAXP) && use_graph(h, alg, p, pl, len, &gg);
     cdc_status s;
     if (pl.sum != SUM_NONE) {
         // the graph's candidate kernel stages up to 1032 blocks past the data
@@ -605,7 +607,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
             if ((s = grow(&h->g_ssuf, &h->g_ssuf_cap, need, false, st)) != CDC_OK) return s;
         }
     }
-    if (graph) return run_graph(h, alg, p, pl, g, gg, out, capacity, d_count, st);
+    if (graph) return run_graph(h, alg, p, pl, g, gg, out, capacity, d_count, st, ctx);
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, st)) != CDC_OK) return s;
     if ((s = grow(&h->hash, &h->hash_cap, items * seg_hash_bytes(), false, st)) != CDC_OK) return s;
     if ((s = grow(&h->plog, &h->plog_cap, items * seg_log_bytes(kLogCap), false, st)) != CDC_OK) return s;

@@ -128,6 +128,7 @@ constexpr uint32_t GID_NONE = 0xFFFFFFFDu;  // no entry
 struct GraphLaunch {
     const uint8_t* base;
     uint64_t lo, hi;         // physical positions of the data (offsets from base)
+    uint64_t flo;            // where the stream's bytes begin (<= lo: MAXP's left context before lo)
     const uint8_t* smax;
     const uint8_t* sarg;
     const uint8_t* ssup;

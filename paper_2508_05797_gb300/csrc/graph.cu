@@ -100,7 +100,7 @@ __device__ unsigned long long g_slow_hop(const GraphLaunch& A, uint32_t id) {
     unsigned long long acc = 0;
     for (;;) {
         uint32_t c;
-        const uint64_t e = cand_next_t<RULE>(S, T, R, P, A.lo, A.hi, y, &c);
+        const uint64_t e = cand_next_t<RULE>(S, T, R, P, A.flo, A.hi, y, &c);
         acc += c;
         if (e >= A.hi) return (acc << 32) | GID_END;
         const uint32_t k2 = g_seg_of(A, e);
@@ -213,8 +213,14 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
     const RawView R{A.base, A.inv};
     const SumView S{A.smax, A.sarg, nullptr, nullptr, 0, 0, A.ssup};
     uint64_t qa0, qb0;
-    cand_source_range<RULE>(P, A.lo, A.hi, &qa0, &qb0);
+    cand_source_range<RULE>(P, A.flo, A.hi, &qa0, &qb0);
     const uint64_t shf = cand_shift<RULE>(P);
+    {
+        // candidates lie past the chain's start (the first slot holds the start)
+        const uint64_t qmin = A.lo + 1 > shf ? A.lo + 1 - shf : 0;
+        if (qa0 < qmin) qa0 = qmin;
+        if (qb0 < qa0) qb0 = qa0;
+    }
     const uint64_t w = A.w;
     // whole blocks of the window common to a block's bytes: RAM [b - K, b),
     // AE [b + 1, b + 1 + K); MAXP reads its targets directly
@@ -325,7 +331,7 @@ __global__ void __launch_bounds__(GC_THREADS) k_gcand(GraphLaunch A) {
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
                         const uint64_t g = (b0 >> 4) + (uint64_t)k;
-                        if ((g << 4) >= (A.lo & ~15ull) && (g << 4) < A.hi) {
+                        if ((g << 4) >= (A.flo & ~15ull) && (g << 4) < A.hi) {
                             const uint4 v = __ldg(reinterpret_cast<const uint4*>(A.base) + g);
                             wd[4 * k] = v.x ^ A.inv; wd[4 * k + 1] = v.y ^ A.inv;
                             wd[4 * k + 2] = v.z ^ A.inv; wd[4 * k + 3] = v.w ^ A.inv;
@@ -742,7 +748,7 @@ __global__ void __launch_bounds__(GL_THREADS, 1) k_glocal(GraphLaunch A) {
         for (uint32_t i = tid; i < n; i += GL_THREADS) {
             const uint64_t y = a + lpos[i];
             uint32_t cnt;
-            const uint32_t k = list_next<RULE>(L, wm, R, P, A.lo, A.hi, y, &cnt);
+            const uint32_t k = list_next<RULE>(L, wm, R, P, A.flo, A.hi, y, &cnt);
             if (k == LIST_GENERIC) {
                 J[i] = GL_PEND;
                 pq[atomicAdd(&s_np, 1u)] = i;
@@ -771,7 +777,7 @@ __global__ void __launch_bounds__(GL_THREADS, 1) k_glocal(GraphLaunch A) {
                 const uint64_t y = a + lpos[i];
                 uint32_t c = 1, ft, jj = GL_EXIT;
                 const long long tg = st ? clock64() : 0;
-                const uint64_t e = w_cand_next<RULE>(S, R, P, A.lo, A.hi, y, &c);
+                const uint64_t e = w_cand_next<RULE>(S, R, P, A.flo, A.hi, y, &c);
                 if (lane != 0) continue;
                 if (st) {
                     const unsigned long long dt = (unsigned long long)(clock64() - tg);
@@ -1043,7 +1049,7 @@ __global__ void __launch_bounds__(GE_THREADS) k_gemit(GraphLaunch A) {
                         for (;;) {
                             uint32_t k;
                             uint64_t d;
-                            const uint64_t e2 = w_advance_far<RULE>(S, R, P, A.lo, A.hi, s2, A.hi, &k, &d);
+                            const uint64_t e2 = w_advance_far<RULE>(S, R, P, A.flo, A.hi, s2, A.hi, &k, &d);
                             for (uint32_t t = 1; t <= k; t++) {
                                 if (lane == 0) buf[held] = s2 + t * d - A.lo;
                                 held++;
@@ -1063,7 +1069,7 @@ __global__ void __launch_bounds__(GE_THREADS) k_gemit(GraphLaunch A) {
                                 break;
                             }
                             s2 = e2;
-                            if (e2 >= A.hi || w_is_cand<RULE>(S, R, P, A.lo, A.hi, e2)) break;
+                            if (e2 >= A.hi || w_is_cand<RULE>(S, R, P, A.flo, A.hi, e2)) break;
                         }
                         e = s2;
                         if (ft != GID_SLOW) nxt = ft;
