@@ -559,6 +559,7 @@ static cdc_status run_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan&
     ga.d_count = d_count;
     ga.ctrl = h->ctrl;
     ga.stats = h->stats ? h->ctrl->stats : nullptr;
+    ga.timeout_ns = (uint64_t)h->timeout_ms * 1000000ull;
     // running maxima inside superblocks (written by the summary kernel)
     if (pl.rule != RULE_MAXP) {
         ga.spre = h->g_spre;

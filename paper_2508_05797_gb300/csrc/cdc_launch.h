@@ -129,6 +129,7 @@ struct GraphLaunch {
     const uint8_t* base;
     uint64_t lo, hi;         // physical positions of the data (offsets from base)
     uint64_t flo;            // where the stream's bytes begin (<= lo: MAXP's left context before lo)
+    uint64_t timeout_ns;     // limit of every wait (the chase kernels' staging copies)
     const uint8_t* smax;
     const uint8_t* sarg;
     const uint8_t* ssup;

@@ -869,15 +869,96 @@ __global__ void __launch_bounds__(GL_THREADS, 1) k_glocal(GraphLaunch A) {
     }
 }
 
+// ---- staged exit tables for the chase ------------------------------------------------
+//
+// The chase kernels (k_gunit, k_gtop, k_gdesc) follow chains hop by hop, each
+// hop a load that depends on the previous one. A CTA first copies the table
+// entries its walks can read (the exits of a unit's segments, or the unit
+// exits of every unit's first segment) into shared memory with coalesced
+// loads, so that the hops themselves read shared memory. Tables that do not
+// fit are read from global memory as before.
+
+constexpr int GU_THREADS = 512;
+constexpr uint32_t GU_MAXP = 256;                  // parts (segments or units) a staged table spans
+constexpr uint32_t GU_ENTRIES = 24576;             // staged entries (8 bytes each)
+int graph_chase_smem() { return (int)(GU_ENTRIES * 8u); }
+
+struct StagedTab {
+    const unsigned long long* ent;  // entries of part j at ent[off[j]], part j = segment k0 + j * step
+    const uint32_t* off;
+    uint32_t k0, step, parts;
+    bool ok;
+};
+
+// Copy the first g_slot_n(k) entries (rounded up to an even count: 16-byte
+// copies) of src[k * cap ...] for the segments k = k0 + j * step (j < parts)
+// into ent, with the bulk-copy engine (one copy per part, completed on the
+// mbarrier `bar`; *phase counts its uses). False (nothing staged) if they do
+// not fit or the copies do not complete in time.
+__device__ bool g_stage(const GraphLaunch& A, const unsigned long long* src, uint32_t k0, uint32_t step,
+                        uint32_t parts, unsigned long long* ent, uint32_t* off, uint64_t* bar, uint32_t* phase) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (parts > GU_MAXP) return false;
+    for (uint32_t j = tid; j < parts; j += nt) off[j + 1] = (g_slot_n(A, k0 + j * step) + 1u) & ~1u;
+    __syncthreads();
+    if (tid == 0) {
+        off[0] = 0;
+        for (uint32_t j = 0; j < parts; j++) off[j + 1] += off[j];
+    }
+    __syncthreads();
+    const uint32_t tot = off[parts];
+    if (tot > GU_ENTRIES) return false;
+    if (tot == 0) return true;
+    if (tid == 0) {
+        // the buffer was last read by ordinary loads: order them before the copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar, tot * 8u);
+        for (uint32_t j = 0; j < parts; j++) {
+            const uint32_t n = off[j + 1] - off[j];
+            if (n) bulk_g2s(ent + off[j], src + (uint64_t)(k0 + j * step) * A.cap, n * 8u, bar);
+        }
+    }
+    const uint32_t par = *phase & 1u;
+    *phase += 1;
+    bool ok = mbar_wait_bounded(bar, par, A.timeout_ns);
+    if (!ok) {
+        // flag it, and let the copies in flight land before the buffer is reused
+        if (tid == 0) atomicOr(&A.ctrl->err, ERR_TIMEOUT);
+        mbar_wait_bounded(bar, par, A.timeout_ns);
+    }
+    return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+// one mbarrier for g_stage, initialised by the CTA
+__device__ __forceinline__ void g_stage_init(uint64_t* bar) {
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+// the table entry of candidate id: staged if id's segment is a staged part
+__device__ __forceinline__ unsigned long long g_tab(const GraphLaunch& A, const StagedTab& T,
+                                                    const unsigned long long* src, uint32_t id) {
+    const uint32_t k = id / A.cap;
+    if (T.ok && k >= T.k0) {
+        const uint32_t d = k - T.k0;
+        if (d % T.step == 0 && d / T.step < T.parts) return T.ent[T.off[d / T.step] + (id - k * A.cap)];
+    }
+    return src[id];
+}
+
 // ---- k_gunit: exits of each unit's first segment past the unit ----------------
 
 template <int RULE>
-__device__ __forceinline__ unsigned long long g_unit_exit(const GraphLaunch& A, uint32_t id) {
+__device__ __forceinline__ unsigned long long g_unit_exit(const GraphLaunch& A, const StagedTab& T, uint32_t id) {
     const uint32_t kend0 = (id / A.cap / A.G + 1) * A.G;
     const uint32_t kend = kend0 < A.nseg ? kend0 : A.nseg;
     unsigned long long acc = 0;
     for (uint32_t guard = 0; id < GID_NONE && id / A.cap < kend; guard++) {
-        const unsigned long long v = g_hop<RULE>(A, id);
+        unsigned long long v = g_tab(A, T, A.cex, id);
+        if ((uint32_t)v == GID_SLOW) v = g_slow_hop<RULE>(A, id);
         if ((uint32_t)v <= id || guard > A.G) {  // ids only grow along a chain, one segment at least
             g_fail(A, id);
             id = GID_END;
@@ -890,31 +971,47 @@ __device__ __forceinline__ unsigned long long g_unit_exit(const GraphLaunch& A, 
 }
 
 template <int RULE>
-__global__ void __launch_bounds__(256) k_gunit(GraphLaunch A) {
-    // (a) every candidate of each unit's first segment
+__global__ void __launch_bounds__(GU_THREADS) k_gunit(GraphLaunch A) {
+    extern __shared__ __align__(16) unsigned long long gu_ent[];
+    __shared__ uint32_t gu_off[GU_MAXP + 1];
+    __shared__ uint64_t gu_bar;
+    g_stage_init(&gu_bar);
+    uint32_t phase = 0;
+    // (a) every candidate of each unit's first segment, over the unit's staged exits
     for (uint32_t u = blockIdx.x; u < A.nunit; u += gridDim.x) {
         const uint32_t k0 = u * A.G;
+        const uint32_t parts = (k0 + A.G < A.nseg ? k0 + A.G : A.nseg) - k0;
+        StagedTab T{gu_ent, gu_off, k0, 1, parts, false};
+        T.ok = g_stage(A, A.cex, k0, 1, parts, gu_ent, gu_off, &gu_bar, &phase);
         const uint32_t n0 = g_slot_n(A, k0);
-        for (uint32_t i = blockIdx.y * blockDim.x + threadIdx.x; i < n0; i += gridDim.y * blockDim.x) {
+        for (uint32_t i = threadIdx.x; i < n0; i += blockDim.x) {
             const uint32_t id = k0 * A.cap + i;
-            A.cux[id] = g_unit_exit<RULE>(A, id);
+            A.cux[id] = g_unit_exit<RULE>(A, T, id);
         }
+        __syncthreads();  // the staged table is replaced by the next unit's
     }
     // (b) the far landings (a chain entering a unit past its first segment)
+    const StagedTab none{nullptr, nullptr, 0, 1, 0, false};
     const unsigned long long nf0 = A.ticket[1];
     const uint32_t nf = nf0 < A.far_cap ? (uint32_t)nf0 : A.far_cap;
-    const uint32_t gt = (blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
-    const uint32_t gn = gridDim.x * gridDim.y * blockDim.x;
-    for (uint32_t f = gt; f < nf; f += gn) {
+    for (uint32_t f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
         const uint32_t id = A.far_list[f];
-        if ((id / A.cap) % A.G != 0) A.cux[id] = g_unit_exit<RULE>(A, id);
+        if ((id / A.cap) % A.G != 0) A.cux[id] = g_unit_exit<RULE>(A, none, id);
     }
 }
 
 // ---- k_gtop: the true chain over the units (or the segments) ----------------------
 
 template <int RULE>
-__global__ void k_gtop(GraphLaunch A) {
+__global__ void __launch_bounds__(GU_THREADS) k_gtop(GraphLaunch A) {
+    extern __shared__ __align__(16) unsigned long long gu_ent[];
+    __shared__ uint32_t gu_off[GU_MAXP + 1];
+    __shared__ uint64_t gu_bar;
+    g_stage_init(&gu_bar);
+    uint32_t phase = 0;
+    // the unit exits of every unit's first segment, staged
+    StagedTab T{gu_ent, gu_off, 0, A.G, A.nunit, false};
+    if (A.nunit > 1) T.ok = g_stage(A, A.cux, 0, A.G, A.nunit, gu_ent, gu_off, &gu_bar, &phase);
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     uint32_t id = 0;  // segment 0, slot 0: the first byte
     unsigned long long off = 0;
@@ -942,10 +1039,14 @@ __global__ void k_gtop(GraphLaunch A) {
             const uint32_t k = id / A.cap, u = k / A.G;
             A.uent[u] = id;
             A.uoff[u] = off;
+            if (k == u * A.G) {
+                next(g_tab(A, T, A.cux, id));
+                continue;
+            }
             // both loads at once: the flag decides which one the hop uses
             const unsigned long long vu = A.cux[id];
             const uint8_t far = A.cfar[id];
-            if (k == u * A.G || far) {
+            if (far) {
                 next(vu);
             } else {
                 const uint32_t kend = (u + 1) * A.G;
@@ -961,25 +1062,37 @@ __global__ void k_gtop(GraphLaunch A) {
 // ---- k_gdesc: each unit's segments ---------------------------------------------------
 
 template <int RULE>
-__global__ void k_gdesc(GraphLaunch A) {
-    if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(GU_THREADS) k_gdesc(GraphLaunch A) {
+    extern __shared__ __align__(16) unsigned long long gu_ent[];
+    __shared__ uint32_t gu_off[GU_MAXP + 1];
+    __shared__ uint64_t gu_bar;
+    g_stage_init(&gu_bar);
+    uint32_t phase = 0;
     for (uint32_t u = blockIdx.x; u < A.nunit; u += gridDim.x) {
         uint32_t id = A.uent[u];
-        if (id >= GID_NONE) continue;
-        unsigned long long off = A.uoff[u];
-        const uint32_t kend = (u + 1) * A.G;
-        for (uint32_t hops = 0; id < GID_NONE && id / A.cap < kend; hops++) {
-            const uint32_t k = id / A.cap;
-            A.sent[k] = id;
-            A.soff[k] = off;
-            const unsigned long long v = g_hop<RULE>(A, id);
-            if ((uint32_t)v <= id || hops > A.G) {
-                g_fail(A, id);
-                break;
+        if (id >= GID_NONE) continue;  // (uniform over the CTA)
+        const uint32_t k0 = u * A.G;
+        const uint32_t parts = (k0 + A.G < A.nseg ? k0 + A.G : A.nseg) - k0;
+        StagedTab T{gu_ent, gu_off, k0, 1, parts, false};
+        T.ok = g_stage(A, A.cex, k0, 1, parts, gu_ent, gu_off, &gu_bar, &phase);
+        if (threadIdx.x == 0) {
+            unsigned long long off = A.uoff[u];
+            const uint32_t kend = (u + 1) * A.G;
+            for (uint32_t hops = 0; id < GID_NONE && id / A.cap < kend; hops++) {
+                const uint32_t k = id / A.cap;
+                A.sent[k] = id;
+                A.soff[k] = off;
+                unsigned long long v = g_tab(A, T, A.cex, id);
+                if ((uint32_t)v == GID_SLOW) v = g_slow_hop<RULE>(A, id);
+                if ((uint32_t)v <= id || hops > A.G) {
+                    g_fail(A, id);
+                    break;
+                }
+                off += v >> 32;
+                id = (uint32_t)v;
             }
-            off += v >> 32;
-            id = (uint32_t)v;
         }
+        __syncthreads();  // the staged table is replaced by the next unit's
     }
 }
 
@@ -1124,6 +1237,9 @@ static int g_allow_smem() {
     return launch_memo(400 + RULE, 0, [](uint32_t) {
         int e = allow_max_smem(k_glocal<RULE>);
         if (e == 0) e = allow_max_smem(k_gemit<RULE>);
+        if (e == 0) e = allow_max_smem(k_gunit<RULE>);
+        if (e == 0) e = allow_max_smem(k_gtop<RULE>);
+        if (e == 0) e = allow_max_smem(k_gdesc<RULE>);
         return e;
     });
 }
@@ -1158,13 +1274,14 @@ static cudaError_t launch_graph_rule(const GraphLaunch& a, const GraphGrids& g, 
     k_glocal<RULE><<<g.local, GL_THREADS, graph_local_smem(RULE, a.cap, a.win), st>>>(a);
     if (ev_mid) cudaEventRecord(ev_mid, st);
     int n = 4;
+    const int csm = graph_chase_smem();
     if (a.nunit > 1) {
-        k_gunit<RULE><<<dim3((unsigned)g.unit, (a.cap + 255) / 256), 256, 0, st>>>(a);
+        k_gunit<RULE><<<g.unit, GU_THREADS, csm, st>>>(a);
         n++;
     }
-    k_gtop<RULE><<<1, 32, 0, st>>>(a);
+    k_gtop<RULE><<<1, GU_THREADS, csm, st>>>(a);
     if (a.nunit > 1) {
-        k_gdesc<RULE><<<g.unit, 32, 0, st>>>(a);
+        k_gdesc<RULE><<<g.unit, GU_THREADS, csm, st>>>(a);
         n++;
     }
     k_gemit<RULE><<<g.emit, GE_THREADS, graph_emit_smem(a.cap), st>>>(a);
