@@ -167,7 +167,7 @@ typedef enum {
                                  16 for MAXP) */
     CDC_OPT_PIPELINE = 9,     /* chain stage of cdc_chunk / cdc_chunk_async /
                                  cdc_chunk_host: 0 = automatic (the candidate
-                                 graph for inputs up to 384 MiB, 768 MiB for
+                                 graph for inputs up to 512 MiB, 768 MiB for
                                  AE, where it applies: RAM and AE-Max with
                                  w >= 64 and min <= w + 1, MAXP with
                                  63 <= w <= 16384; else speculation),

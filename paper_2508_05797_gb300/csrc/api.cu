@@ -408,7 +408,7 @@ static Geo geometry(const uint8_t* data, uint64_t len) {
 
 // ---- candidate-graph chain stage (graph.cu) ------------------------------------
 
-static constexpr uint64_t kGraphAutoMax = 384ull << 20;
+static constexpr uint64_t kGraphAutoMax = 512ull << 20;
 static constexpr uint64_t kGraphAutoMaxAE = 768ull << 20;
 
 struct GraphGeo {
@@ -426,8 +426,8 @@ struct GraphGeo {
 static bool use_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan& pl, uint64_t len, GraphGeo* gg) {
     if (h->pipeline == 1 || h->force_bytes) return false;
     // automatic: the graph for inputs up to kGraphAutoMax (kGraphAutoMaxAE for
-    // AE), where it measured faster on the mixed stream at 4, 8 and 16 KiB
-    // means; beyond that the speculative segments are faster
+    // AE), where it measured as fast or faster on the mixed stream at 4 and
+    // 16 KiB means; at 1 GiB the speculative segments are faster
     if (h->pipeline == 0 && len > (pl.rule == RULE_AE ? kGraphAutoMaxAE : kGraphAutoMax)) return false;
     switch (pl.rule) {
     case RULE_RAM:
