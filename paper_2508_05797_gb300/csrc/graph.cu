@@ -39,8 +39,10 @@
 namespace cdc {
 
 constexpr int GC_THREADS = 256;  // k_gcand
-constexpr int GL_THREADS = 512;  // k_gjump
-constexpr int GL_PER = 8;        // candidates per thread in the jumping rounds
+// k_glocal runs 512 threads per segment when a segment has up to 4096 slots,
+// 256 (two CTAs per SM) when it has up to 2048; each thread takes up to
+// GL_PER candidates in the jumping rounds
+constexpr int GL_PER = 8;
 constexpr uint32_t GL_EXIT = 0xFFFFFFFFu;
 constexpr uint32_t GL_PEND = 0xFFFFFFFEu;  // F not yet known (k_glocal)
 constexpr int GE_BUF = 256;      // k_gemit: boundaries buffered before a store
@@ -657,8 +659,8 @@ __device__ __forceinline__ void g_copy_u8(uint8_t* dst, const uint8_t* src, uint
     for (uint32_t i = nv * 16 + (uint32_t)tid; i < n; i += (uint32_t)nt) dst[i] = src[i];
 }
 
-template <int RULE>
-__global__ void __launch_bounds__(GL_THREADS, 1) k_glocal(GraphLaunch A) {
+template <int RULE, int GL_THREADS>
+__global__ void __launch_bounds__(GL_THREADS, 512 / GL_THREADS) k_glocal(GraphLaunch A) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t cap = A.cap;
     uint32_t* lpos = reinterpret_cast<uint32_t*>(smem);  // own then next segment's candidates - segment start
@@ -1235,7 +1237,8 @@ __global__ void __launch_bounds__(GE_THREADS) k_gemit(GraphLaunch A) {
 template <int RULE>
 static int g_allow_smem() {
     return launch_memo(400 + RULE, 0, [](uint32_t) {
-        int e = allow_max_smem(k_glocal<RULE>);
+        int e = allow_max_smem(k_glocal<RULE, 512>);
+        if (e == 0) e = allow_max_smem(k_glocal<RULE, 256>);
         if (e == 0) e = allow_max_smem(k_gemit<RULE>);
         if (e == 0) e = allow_max_smem(k_gunit<RULE>);
         if (e == 0) e = allow_max_smem(k_gtop<RULE>);
@@ -1250,8 +1253,12 @@ static int g_occ_local(uint32_t key) {
     return launch_memo(410 + RULE, key, [](uint32_t kk) {
         const uint32_t cap = kk >> 16, win = (kk & 0xFFFFu) * 16;
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_glocal<RULE>, GL_THREADS,
-                                                      graph_local_smem(RULE, cap, win));
+        if (cap <= 2048)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_glocal<RULE, 256>, 256,
+                                                          graph_local_smem(RULE, cap, win));
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_glocal<RULE, 512>, 512,
+                                                          graph_local_smem(RULE, cap, win));
         return n > 0 ? n : 1;
     });
 }
@@ -1271,7 +1278,10 @@ static cudaError_t launch_graph_rule(const GraphLaunch& a, const GraphGrids& g, 
     const int set = g_allow_smem<RULE>();
     if (set != (int)cudaSuccess) return (cudaError_t)set;
     k_gcand<RULE><<<g.cand, GC_THREADS, 0, st>>>(a);
-    k_glocal<RULE><<<g.local, GL_THREADS, graph_local_smem(RULE, a.cap, a.win), st>>>(a);
+    if (a.cap <= 2048)
+        k_glocal<RULE, 256><<<g.local, 256, graph_local_smem(RULE, a.cap, a.win), st>>>(a);
+    else
+        k_glocal<RULE, 512><<<g.local, 512, graph_local_smem(RULE, a.cap, a.win), st>>>(a);
     if (ev_mid) cudaEventRecord(ev_mid, st);
     int n = 4;
     const int csm = graph_chase_smem();
