@@ -184,12 +184,14 @@ __global__ void __launch_bounds__(S1_THREADS) k_summary_max(SumLaunch a) {
 
 // ---- MAXP targets --------------------------------------------------------------
 
-constexpr int MP_THREADS = 256;
+// one thread per stage block (the tile's 256 blocks and up to 32 halo blocks)
+// in the block-key pass, so that the halo costs no second round
+constexpr int MP_THREADS = 288;
 constexpr int MP_TILE_BLOCKS = 256;  // 16 KiB of targets per tile
 
 // Dynamic shared memory: 2 stages of (MP_TILE_BLOCKS + 2*hb) * 64 bytes, then
 // per-stage-block max / first-position arrays (and one spare), then 2 mbarriers.
-__global__ void __launch_bounds__(MP_THREADS, 6) k_summary_maxp(SumLaunch a) {
+__global__ void __launch_bounds__(MP_THREADS, 5) k_summary_maxp(SumLaunch a) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
     const uint32_t hb = a.halo_blocks;
@@ -270,8 +272,8 @@ __global__ void __launch_bounds__(MP_THREADS, 6) k_summary_maxp(SumLaunch a) {
         // 2) prefilter, one thread per tile block: the blocks within K of it lie
         // inside the window wherever the maximum sits in its block, so none of
         // them may reach its maximum. Survivors (a small share) are listed.
-        static_assert(MP_TILE_BLOCKS == MP_THREADS, "one tile block per thread");
-        {
+        static_assert(MP_THREADS >= MP_TILE_BLOCKS && MP_THREADS % 32 == 0, "one tile block per thread");
+        if (tid < MP_TILE_BLOCKS) {
             const uint32_t lb = (uint32_t)tid;
             const uint64_t gb = t * MP_TILE_BLOCKS + lb;
             const uint32_t sbi = hb + lb;
@@ -349,7 +351,15 @@ __global__ void __launch_bounds__(MP_THREADS, 6) k_summary_maxp(SumLaunch a) {
             if (lane == 0) qres[lb] = bal == 0 ? 1 : 0;
         }
         __syncthreads();
-        {
+        // the stage's bytes are no longer read: refill it with the tile after next
+        if (tid == 0) {
+            uint64_t tn = t + 2 * g;
+            if (tn < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(tn, s);
+            }
+        }
+        if (tid < MP_TILE_BLOCKS) {  // (whole warps)
             const uint32_t lb = (uint32_t)tid;
             const uint64_t gb = t * MP_TILE_BLOCKS + lb;
             const uint32_t state = tstate[lb];
@@ -367,10 +377,6 @@ __global__ void __launch_bounds__(MP_THREADS, 6) k_summary_maxp(SumLaunch a) {
             supcnt[tid] = 0;
         }
         __syncthreads();
-        if (tid == 0) {
-            uint64_t tn = t + 2 * g;
-            if (tn < ntiles) issue(tn, s);
-        }
     }
 }
 
