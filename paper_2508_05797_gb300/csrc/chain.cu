@@ -196,10 +196,19 @@ __device__ Geo seg_geo(const ChainLaunch& A, uint64_t item, int lane, int bound)
 // one 64-bit word, so a chain that finds its position already present learns
 // at once which chain got there first.
 
-constexpr int HSLOTS = 2048;
-constexpr int HFILL = 1400;  // stop inserting beyond this many entries
+// Per segment, a position hash of 2^BITS slots (stop inserting beyond FILL
+// entries). RAM and AE chains need the 2048-slot table to find their merges;
+// MAXP merges within a chunk and takes 1024 slots, which leaves room for
+// more CTAs per SM. Every segment's hash has HSTRIDE slots in HBM.
+template <int RULE>
+struct HashCfg {
+    static constexpr int BITS = RULE == RULE_MAXP ? 10 : 11;
+    static constexpr int SLOTS = 1 << BITS;
+    static constexpr int FILL = BITS == 11 ? 1400 : SLOTS * 11 / 16;
+};
+constexpr int HSTRIDE = 2048;
 
-size_t seg_hash_bytes() { return (size_t)HSLOTS * sizeof(unsigned long long); }
+size_t seg_hash_bytes() { return (size_t)HSTRIDE * sizeof(unsigned long long); }
 
 // ---- per-segment step log -------------------------------------------------------
 // Every step of every speculative chain of a segment, in the order taken:
@@ -224,14 +233,18 @@ __device__ __forceinline__ void log_step(const ChainLaunch& A, uint64_t item, un
     }
 }
 
-__device__ __forceinline__ uint32_t hslot(uint32_t key) { return (key * 2654435761u) >> 21; }  // 11 bits
+template <int RULE>
+__device__ __forceinline__ uint32_t hslot(uint32_t key) {
+    return (key * 2654435761u) >> (32 - HashCfg<RULE>::BITS);
+}
 constexpr uint32_t H_INSERTED = 0xFFFFFFFFu, H_FULL = 0xFFFFFFFEu;
 
 // insert; returns H_INSERTED, H_FULL, or the value already stored for key
+template <int RULE>
 __device__ __forceinline__ uint32_t hinsert(unsigned long long* ht, unsigned int* fill, uint32_t key, uint32_t val) {
-    if (*reinterpret_cast<volatile unsigned int*>(fill) >= (unsigned)HFILL) return H_FULL;
+    if (*reinterpret_cast<volatile unsigned int*>(fill) >= (unsigned)HashCfg<RULE>::FILL) return H_FULL;
     const unsigned long long ent = ((unsigned long long)key << 32) | val;
-    uint32_t s = hslot(key);
+    uint32_t s = hslot<RULE>(key);
     for (int i = 0; i < 64; i++) {
         unsigned long long prev = atomicCAS(&ht[s], 0ull, ent);
         if (prev == 0ull) {
@@ -239,19 +252,20 @@ __device__ __forceinline__ uint32_t hinsert(unsigned long long* ht, unsigned int
             return H_INSERTED;
         }
         if ((uint32_t)(prev >> 32) == key) return (uint32_t)prev;
-        s = (s + 1) & (HSLOTS - 1);
+        s = (s + 1) & (HashCfg<RULE>::SLOTS - 1);
     }
     return H_FULL;
 }
 
 // value stored for key, or ~0u
+template <int RULE>
 __device__ __forceinline__ uint32_t hfind(const unsigned long long* ht, uint32_t key) {
-    uint32_t s = hslot(key);
+    uint32_t s = hslot<RULE>(key);
     for (int i = 0; i < 64; i++) {
         const unsigned long long e = ht[s];
         if ((uint32_t)(e >> 32) == key) return (uint32_t)e;
         if (e == 0ull) return ~0u;
-        s = (s + 1) & (HSLOTS - 1);
+        s = (s + 1) & (HashCfg<RULE>::SLOTS - 1);
     }
     return ~0u;
 }
@@ -281,8 +295,9 @@ __device__ bool wait_flag_thread(const unsigned int* f, uint32_t epoch, const Ch
 
 constexpr int KS = 1;          // per-thread steps per round before the live chains are compacted
 
+template <int RULE>
 struct SpecShared {
-    unsigned long long ht[HSLOTS];
+    unsigned long long ht[HashCfg<RULE>::SLOTS];
     unsigned int fill;
     unsigned int log_n;            // records in the segment's step log
     unsigned int nq;               // live chains (compacted into threads [0, nq))
@@ -303,7 +318,7 @@ struct SpecShared {
 template <int RULE>
 __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
     extern __shared__ __align__(16) uint8_t dsm[];  // staged summaries: m[win], a[win]
-    __shared__ SpecShared sh;
+    __shared__ SpecShared<RULE> sh;
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t epoch = ld_volatile(&A.ctrl->epoch);
     const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
@@ -316,7 +331,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
             sh.item = atomicAdd(&A.ctrl->ticket, 1ull);
             sh.ok = ld_volatile(&A.ctrl->err) == 0;
         }
-        for (int i = tid; i < HSLOTS; i += NL) sh.ht[i] = 0ull;
+        for (int i = tid; i < HashCfg<RULE>::SLOTS; i += NL) sh.ht[i] = 0ull;
         if (tid == 0) {
             sh.fill = 0;
             sh.log_n = 0;
@@ -421,7 +436,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                     bool alive = true, recl = rec;
                     for (int r = 0; r < KS; r++) {
                         if (recl) {
-                            const uint32_t hr = c < 0xFFFFu ? hinsert(sh.ht, &sh.fill, (uint32_t)(s - seg_lo) + 1u,
+                            const uint32_t hr = c < 0xFFFFu ? hinsert<RULE>(sh.ht, &sh.fill, (uint32_t)(s - seg_lo) + 1u,
                                                                        (l << 16) | c)
                                                             : H_FULL;
                             if (hr == H_FULL) {
@@ -474,7 +489,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                 if (tid == 0) {
                     stat_add(A, STAT_SEGMENTS, 1);
                     stat_add(A, STAT_SURVIVORS, sh.nq);
-                    if (sh.fill >= (unsigned)HFILL) stat_add(A, STAT_HASH_FULL, 1);
+                    if (sh.fill >= (unsigned)HashCfg<RULE>::FILL) stat_add(A, STAT_HASH_FULL, 1);
                 }
             }
             // the last chains, one warp each (every step shared by the 32 lanes);
@@ -492,7 +507,7 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
                     if (recq) {
                         uint32_t hr = H_FULL;
                         if (lane == 0 && cc < 0xFFFFu)
-                            hr = hinsert(sh.ht, &sh.fill, (uint32_t)(v - seg_lo) + 1u, (l << 16) | cc);
+                            hr = hinsert<RULE>(sh.ht, &sh.fill, (uint32_t)(v - seg_lo) + 1u, (l << 16) | cc);
                         hr = __shfl_sync(FULL, hr, 0);
                         if (hr == H_FULL) {
                             recq = false;
@@ -555,9 +570,9 @@ __global__ void __launch_bounds__(NL) k_spec(ChainLaunch A) {
         }
         // the position hash goes to HBM for the stitch kernels
         if (!first && !empty) {
-            uint4* dst = reinterpret_cast<uint4*>(A.hash + item * (uint64_t)HSLOTS);
+            uint4* dst = reinterpret_cast<uint4*>(A.hash + item * (uint64_t)HSTRIDE);
             const uint4* src = reinterpret_cast<const uint4*>(sh.ht);
-            for (int i = tid; i < HSLOTS / 2; i += NL) dst[i] = src[i];
+            for (int i = tid; i < HashCfg<RULE>::SLOTS / 2; i += NL) dst[i] = src[i];
         }
         __syncthreads();
         if (!sh.ok) break;
@@ -594,7 +609,7 @@ __device__ uint32_t stitch_walk(const ChainLaunch& A, const SumView& S, const Ra
     uint64_t v = e;
     uint32_t ne = 0, res = STAB_UNKNOWN;
     while (v < seg_hi) {
-        const uint32_t hv = hfind(ht, (uint32_t)(v - seg_lo) + 1u);
+        const uint32_t hv = hfind<RULE>(ht, (uint32_t)(v - seg_lo) + 1u);
         if (hv != ~0u) {
             const uint32_t m = hv >> 16, idx = hv & 0xFFFFu;
             res = stab_enc(m, ne + cnt[m] - idx + (last ? 1u : 0u));
@@ -638,20 +653,22 @@ __device__ uint32_t stitch_walk(const ChainLaunch& A, const SumView& S, const Ra
     return res;
 }
 
+template <int RULE>
 struct StitchShared {
-    unsigned long long ht[HSLOTS];
+    unsigned long long ht[HashCfg<RULE>::SLOTS];
     unsigned long long X[NL];
     unsigned int cnt[NL];
     int ok;
 };
 
 // Load a segment's hash, exits and counts into shared memory.
-__device__ __forceinline__ void load_segment(const ChainLaunch& A, uint64_t item, StitchShared& sh) {
+template <int RULE>
+__device__ __forceinline__ void load_segment(const ChainLaunch& A, uint64_t item, StitchShared<RULE>& sh) {
     const int tid = threadIdx.x;
-    const uint4* src = reinterpret_cast<const uint4*>(A.hash + item * (uint64_t)HSLOTS);
+    const uint4* src = reinterpret_cast<const uint4*>(A.hash + item * (uint64_t)HSTRIDE);
     uint4* dst = reinterpret_cast<uint4*>(sh.ht);
-    constexpr int PER = HSLOTS / 2 / NL;  // 16-byte loads per thread, all in flight at once
-    static_assert(HSLOTS / 2 % NL == 0, "hash rows split evenly over the threads");
+    constexpr int PER = HashCfg<RULE>::SLOTS / 2 / NL;  // 16-byte loads per thread, all in flight at once
+    static_assert(HashCfg<RULE>::SLOTS / 2 % NL == 0, "hash rows split evenly over the threads");
     uint4 r[PER];
 #pragma unroll
     for (int k = 0; k < PER; k++) r[k] = src[tid + k * NL];
@@ -667,7 +684,7 @@ __device__ __forceinline__ void load_segment(const ChainLaunch& A, uint64_t item
 // for every segment; empty segments take their predecessor's exits.
 template <int RULE>
 __global__ void __launch_bounds__(NL) k_stitch(ChainLaunch A) {
-    __shared__ StitchShared sh;
+    __shared__ StitchShared<RULE> sh;
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t epoch = ld_volatile(&A.ctrl->epoch);
     const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
@@ -739,7 +756,7 @@ __global__ void __launch_bounds__(NL) k_stitch(ChainLaunch A) {
 // resolution kernels need not walk whole segments.
 template <int RULE>
 __global__ void __launch_bounds__(NL) k_ures(ChainLaunch A) {
-    __shared__ StitchShared sh;
+    __shared__ StitchShared<RULE> sh;
     __shared__ int any;
     const int tid = threadIdx.x, lane = tid & 31;
     const uint64_t n_items = A.n_items_dev ? *reinterpret_cast<const volatile unsigned long long*>(A.n_items_dev)
@@ -1193,7 +1210,7 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
             }
             const uint32_t ln = st->log_n;
             const bool use_log = ln <= A.logcap;
-            const unsigned long long* ht = A.hash + item * (uint64_t)HSLOTS;
+            const unsigned long long* ht = A.hash + item * (uint64_t)HSTRIDE;
             const ulonglong2* lg = reinterpret_cast<const ulonglong2*>(A.plog) + item * (uint64_t)(A.logcap + SWCAP);
             constexpr uint64_t POS = (1ull << 57) - 1;
             while (v < seg_hi) {
@@ -1204,7 +1221,7 @@ __global__ void __launch_bounds__(32) k_output(ChainLaunch A) {
                     if (first) {
                         m = v == flo ? 0 : -1;
                     } else {
-                        const uint32_t hv = hfind(ht, (uint32_t)(v - seg_lo) + 1u);
+                        const uint32_t hv = hfind<RULE>(ht, (uint32_t)(v - seg_lo) + 1u);
                         m = hv == ~0u ? -1 : (int)(hv >> 16);
                     }
                 }
