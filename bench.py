@@ -925,11 +925,18 @@ def main():
     iso_achieved = n / (iso_spec_ms / 1e3) / 1e9
     iso_sum_ms = sum(r["summary_ms"] for r in iso) / max(1, len(iso))
     sum_achieved = n / (iso_sum_ms / 1e3) / 1e9
-    dpb = profile_traffic()
+    # which chain stage the calls took (the automatic policy: the candidate
+    # graph up to 512 MiB, 768 MiB for AE; speculation beyond)
+    stages = sorted({ck.last_stage() for ck in handles})
+    graph = stages == [2]
+    dpb = profile_traffic() if stages == [1] else None
+    kname = ("k_gcand + k_glocal (chain stage: candidates, F and pointer jumping of the candidate graph)" if graph
+             else "k_spec (chain stage: speculative chains), the largest share of the step's device time"
+             if stages == [1] else "k_spec or k_gcand + k_glocal (chain stage; the calls took both stages)")
     roofline = {"bound": "hbm", "achieved": round(iso_achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(iso_achieved / peak, 4), "traffic": int(dpb * n) if dpb is not None else None,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-                "kernel": "k_spec (chain stage: speculative chains), the largest share of the step's device time",
+                "kernel": kname, "chain_stage": "graph" if graph else "speculation" if stages == [1] else "both",
                 "algorithmic_bytes_per_launch": n, "avg_launch_ms": round(iso_spec_ms, 4),
                 "launch_times": "each call alone on one stream, CUDA events around the kernel",
                 "limited_by": "latency of dependent chain steps (its DRAM traffic is `traffic`)",

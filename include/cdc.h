@@ -235,6 +235,11 @@ CDC_API cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream stre
 /* Number of kernels the last call launched. */
 CDC_API cdc_status cdc_last_launches(cdc_handle h, int* launches);
 
+/* Chain stage the last call on the handle used (CDC_OPT_PIPELINE 0 chooses
+ * per call): 1 = speculative segments, 2 = the candidate graph, 0 before the
+ * first call. Host-side bookkeeping only; no synchronisation. */
+CDC_API cdc_status cdc_last_stage(cdc_handle h, int* stage);
+
 /* ---- chunking without any allocation --------------------------------------
  *
  * The paper has no counterpart: it is a property of this library's interface,

@@ -83,6 +83,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             "cdc_get_option": ([vp, i32, ctypes.POINTER(i64)], i32),
             "cdc_last_timing": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)], i32),
             "cdc_last_launches": ([vp, ctypes.POINTER(i32)], i32),
+            "cdc_last_stage": ([vp, ctypes.POINTER(i32)], i32),
             "cdc_profile_collect": ([vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(i64)], i32),
@@ -118,7 +119,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return ["cdc_create", "cdc_destroy", "cdc_chunk", "cdc_chunk_async", "cdc_chunk_batch", "cdc_chunk_host",
             "cdc_reserve", "cdc_sync_status", "cdc_set_option", "cdc_get_option", "cdc_last_timing",
-            "cdc_last_launches", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_ebs", "cdc_rs", "cdc_fingerprint", "cdc_byte_shares",
+            "cdc_last_launches", "cdc_last_stage", "cdc_profile_collect", "cdc_stats", "cdc_chunk_static", "cdc_autotune", "cdc_ebs", "cdc_rs", "cdc_fingerprint", "cdc_byte_shares",
             "cdc_size_histogram", "cdc_feed_create", "cdc_feed_push",
             "cdc_feed_position", "cdc_feed_reset", "cdc_feed_destroy", "cdc_server_create", "cdc_server_submit",
             "cdc_server_poll", "cdc_server_clock", "cdc_server_destroy", "cdc_status_string"]
@@ -191,6 +192,12 @@ class Chunker:
     def last_launches(self) -> int:
         n = ctypes.c_int()
         _check(self.lib.cdc_last_launches(self.h, ctypes.byref(n)))
+        return n.value
+
+    def last_stage(self) -> int:
+        """Chain stage of the last call: 1 speculation, 2 candidate graph (cdc_last_stage)."""
+        n = ctypes.c_int()
+        _check(self.lib.cdc_last_stage(self.h, ctypes.byref(n)))
         return n.value
 
     def profile_collect(self):

@@ -85,6 +85,7 @@ struct cdc_handle_s {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // start, summaries done, end, speculation done
     bool timed = false;
     int launches = 0;
+    int stage = 0;  // chain stage of the last single-stream call: 1 speculation, 2 candidate graph
     // profiling ring: 4 events (as ev[]) for each of up to PROF_CAP calls
     static constexpr int PROF_CAP = 1024;
     int64_t profile = 0;
@@ -608,6 +609,7 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
             if ((s = grow(&h->g_ssuf, &h->g_ssuf_cap, need, false, st)) != CDC_OK) return s;
         }
     }
+    h->stage = graph ? 2 : 1;
     if (graph) return run_graph(h, alg, p, pl, g, gg, out, capacity, d_count, st, ctx);
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, st)) != CDC_OK) return s;
     if ((s = grow(&h->hash, &h->hash_cap, items * seg_hash_bytes(), false, st)) != CDC_OK) return s;
@@ -970,6 +972,12 @@ extern "C" cdc_status cdc_last_timing(cdc_handle h, float* summary_ms, float* ch
 extern "C" cdc_status cdc_last_launches(cdc_handle h, int* launches) {
     if (!h || !launches) return CDC_ERR_INVALID;
     *launches = h->launches;
+    return CDC_OK;
+}
+
+extern "C" cdc_status cdc_last_stage(cdc_handle h, int* stage) {
+    if (!h || !stage) return CDC_ERR_INVALID;
+    *stage = h->stage;
     return CDC_OK;
 }
 
