@@ -136,3 +136,16 @@ def test_graph_equals_speculation_on_random_params(ck):
             with _with(ck, pipeline=pipe):
                 got = gpu_chunk(ck, data, alg, w, mn, mx, offset=t % 64)
             assert np.array_equal(got, exp), (alg, w, mn, mx, pipe)
+
+
+def test_last_stage_reports_the_chain_stage(ck):
+    """cdc_last_stage names the chain stage a call took: forced either way,
+    and the automatic choice (the graph for a 4 MiB RAM call; speculation for
+    AE-Min, which takes the graph only when forced)."""
+    data = synth.uniform(1, 4 * MIB)
+    for pipe, stage in ((1, 1), (2, 2), (0, 2)):
+        with _with(ck, pipeline=pipe):
+            gpu_chunk(ck, data, "ram", 700, 128, 8192)
+            assert ck.last_stage() == stage, (pipe, ck.last_stage())
+    gpu_chunk(ck, data, "ae_min", 700, 128, 8192)
+    assert ck.last_stage() == 1
