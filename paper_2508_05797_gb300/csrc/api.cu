@@ -423,10 +423,10 @@ struct GraphGeo {
 // Does the call take the candidate graph, and with which geometry? The graph
 // needs every natural cut to be a candidate: min <= w + 1 for RAM and AE (the
 // cut never depends on min), w >= 64 so that the block rules apply, MAXP from
-// block targets. Segments of S >= max bytes (64 KiB below 256 MiB, 128 KiB
-// from there: on 16 MiB of the mixed stream 128 KiB was 1.3x slower for AE, on
-// uniform bytes 3% faster), S / 32 candidate slots each (a multiple of 16);
-// units of about sqrt(segments) segments.
+// block targets. Segments of S >= max bytes (64 KiB below 64 MiB, where 128 KiB
+// was up to 1.3x slower on 16 MiB of the mixed stream; see below), S / 32
+// candidate slots each (a multiple of 16, at most 4096); units of about
+// sqrt(segments) segments.
 static bool use_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan& pl, uint64_t len, GraphGeo* gg) {
     if (h->pipeline == 1 || h->force_bytes) return false;
     // automatic: the graph for inputs up to kGraphAutoMax (kGraphAutoMaxAE for
@@ -442,7 +442,14 @@ static bool use_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan& pl, u
     case RULE_MAXP: break;
     default: return false;
     }
-    uint64_t S = h->graph_seg ? (uint64_t)h->graph_seg : (len >= (256ull << 20) ? (128u << 10) : (64u << 10));
+    // segment size: 64 KiB below 64 MiB, 128 KiB above (10% faster for RAM at 64
+    // and 128 MiB of the mixed stream, AE unchanged); MAXP, whose targets are
+    // sparse, 256 KiB from 128 MiB (5-12% faster). Larger RAM/AE segments
+    // overflow their slots on text-like content.
+    uint64_t S = 64u << 10;
+    if (len >= (64ull << 20)) S = 128u << 10;
+    if (pl.rule == RULE_MAXP && len >= (128ull << 20)) S = 256u << 10;
+    if (h->graph_seg) S = (uint64_t)h->graph_seg;
     const uint64_t mx4k = ((uint64_t)p.max + 4095) & ~4095ull;
     if (S < mx4k) S = mx4k;
     if (S > (64ull << 20)) return false;
