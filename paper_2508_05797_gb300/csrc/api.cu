@@ -479,11 +479,23 @@ static bool use_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan& pl, u
     return true;
 }
 
-static cdc_status run_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan& pl, const Geo& g,
-                            const GraphGeo& gg, uint64_t* out, uint64_t capacity, uint64_t* d_count,
-                            cudaStream_t st, uint64_t ctx) {
-    (void)alg;
+// far landings listed per call (exits more than one segment ahead)
+static size_t graph_far_cap(const GraphGeo& gg) { return (size_t)gg.nseg * 64 + 1024; }
+
+// The candidate graph's workspace for geometry gg over summaries of nblk_pad
+// blocks and nsup superblocks (the candidate kernel stages up to 1032 blocks
+// past the data, so the block arrays get 2112 blocks of room).
+static cdc_status graph_grow(cdc_handle h, const Plan& pl, const GraphGeo& gg, uint64_t nblk_pad, uint64_t nsup,
+                             cudaStream_t st) {
     cdc_status s;
+    const size_t need = nblk_pad + 2112;
+    if ((s = grow(&h->smax, &h->sum_cap, need, false, st)) != CDC_OK) return s;
+    if (pl.sum != SUM_MAXP && (s = grow(&h->sarg, &h->sarg_cap, need, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->ssup, &h->ssup_cap, nsup + 64, false, st)) != CDC_OK) return s;
+    if (pl.rule != RULE_MAXP) {
+        if ((s = grow(&h->g_spre, &h->g_spre_cap, need, false, st)) != CDC_OK) return s;
+        if ((s = grow(&h->g_ssuf, &h->g_ssuf_cap, need, false, st)) != CDC_OK) return s;
+    }
     const size_t slots = (size_t)gg.nseg * gg.cap;
     if ((s = grow(&h->g_cpos, &h->g_cpos_cap, slots, false, st)) != CDC_OK) return s;
     if ((s = grow(&h->g_cval, &h->g_cval_cap, slots, false, st)) != CDC_OK) return s;
@@ -496,10 +508,18 @@ static cdc_status run_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan&
     if ((s = grow(&h->g_soff, &h->g_soff_cap, (size_t)gg.nseg, false, st)) != CDC_OK) return s;
     if ((s = grow(&h->g_uex, &h->g_uex_cap, slots, false, st)) != CDC_OK) return s;
     if ((s = grow(&h->g_cfar, &h->g_cfar_cap, slots, false, st)) != CDC_OK) return s;
-    const size_t far_cap = (size_t)gg.nseg * 64 + 1024;
-    if ((s = grow(&h->g_far, &h->g_far_cap, far_cap, false, st)) != CDC_OK) return s;
+    if ((s = grow(&h->g_far, &h->g_far_cap, graph_far_cap(gg), false, st)) != CDC_OK) return s;
     if ((s = grow(&h->g_uent, &h->g_uent_cap, (size_t)gg.nunit, false, st)) != CDC_OK) return s;
     if ((s = grow(&h->g_uoff, &h->g_uoff_cap, (size_t)gg.nunit, false, st)) != CDC_OK) return s;
+    return CDC_OK;
+}
+
+static cdc_status run_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan& pl, const Geo& g,
+                            const GraphGeo& gg, uint64_t* out, uint64_t capacity, uint64_t* d_count,
+                            cudaStream_t st, uint64_t ctx) {
+    (void)alg;
+    cdc_status s;
+    if ((s = graph_grow(h, pl, gg, g.nblk_pad, g.nsup, st)) != CDC_OK) return s;
     h->launches = 0;
     const bool rec = !capturing(st);
     h->timed = false;
@@ -560,7 +580,7 @@ static cdc_status run_graph(cdc_handle h, cdc_alg alg, cdc_params p, const Plan&
     ga.cux = h->g_uex;
     ga.cfar = h->g_cfar;
     ga.far_list = h->g_far;
-    ga.far_cap = (uint32_t)far_cap;
+    ga.far_cap = (uint32_t)graph_far_cap(gg);
     ga.uent = h->g_uent;
     ga.uoff = h->g_uoff;
     ga.sent = h->g_sent;
@@ -608,19 +628,14 @@ static cdc_status run(cdc_handle h, cdc_alg alg, cdc_params p, const uint8_t* da
     // (a left context only exists for MAXP, whose targets may use it as window bytes)
     const bool graph = !batch && (ctx == 0 || pl.rule == RULE_MAXP) && use_graph(h, alg, p, pl, len, &gg);
     cdc_status s;
+    h->stage = graph ? 2 : 1;
+    if (graph) return run_graph(h, alg, p, pl, g, gg, out, capacity, d_count, st, ctx);
     if (pl.sum != SUM_NONE) {
-        // the graph's candidate kernel stages up to 1032 blocks past the data
-        const size_t need = g.nblk_pad + (graph ? 2112 : 64);
+        const size_t need = g.nblk_pad + 64;
         if ((s = grow(&h->smax, &h->sum_cap, need, false, st)) != CDC_OK) return s;
         if (pl.sum != SUM_MAXP && (s = grow(&h->sarg, &h->sarg_cap, need, false, st)) != CDC_OK) return s;
         if ((s = grow(&h->ssup, &h->ssup_cap, g.nsup + 64, false, st)) != CDC_OK) return s;
-        if (graph && pl.rule != RULE_MAXP) {
-            if ((s = grow(&h->g_spre, &h->g_spre_cap, need, false, st)) != CDC_OK) return s;
-            if ((s = grow(&h->g_ssuf, &h->g_ssuf_cap, need, false, st)) != CDC_OK) return s;
-        }
     }
-    h->stage = graph ? 2 : 1;
-    if (graph) return run_graph(h, alg, p, pl, g, gg, out, capacity, d_count, st, ctx);
     if ((s = grow(&h->st, &h->st_cap, items * seg_state_bytes(), true, st)) != CDC_OK) return s;
     if ((s = grow(&h->hash, &h->hash_cap, items * seg_hash_bytes(), false, st)) != CDC_OK) return s;
     if ((s = grow(&h->plog, &h->plog_cap, items * seg_log_bytes(kLogCap), false, st)) != CDC_OK) return s;
@@ -958,6 +973,12 @@ extern "C" cdc_status cdc_reserve(cdc_handle h, cdc_alg alg, cdc_params p, size_
         if ((s = grow(&h->item_off, &h->files_cap, n_files + 1, false, 0)) != CDC_OK) return s;
         if ((s = grow(&h->scan_tmp, &h->scan_cap, batch_scan_tmp_elems(n_files), false, 0)) != CDC_OK) return s;
         if ((s = grow(&h->item_file, &h->item_file_cap, items, false, 0)) != CDC_OK) return s;
+    } else {
+        // a single stream may take the candidate graph (with the handle's options as they are now)
+        GraphGeo gg;
+        if (len && use_graph(h, alg, p, pl, len, &gg) &&
+            (s = graph_grow(h, pl, gg, nblk_pad, len / 4096 + 2, 0)) != CDC_OK)
+            return s;
     }
     return CDC_OK;
 }

@@ -149,3 +149,36 @@ def test_last_stage_reports_the_chain_stage(ck):
             assert ck.last_stage() == stage, (pipe, ck.last_stage())
     gpu_chunk(ck, data, "ae_min", 700, 128, 8192)
     assert ck.last_stage() == 1
+
+
+@pytest.mark.parametrize("alg", ["ram", "ae", "maxp"])
+def test_capture_after_reserve_without_a_warm_up_call(alg):
+    """cdc_reserve sizes the candidate graph's workspace too, so a fresh
+    handle's first cdc_chunk_async can be captured into a CUDA graph; the
+    replays equal the oracle."""
+    import torch
+    from paper_2508_05797_gb300 import Chunker
+    data = synth.mixed_range(2, 64 * MIB, 3 * MIB, 6 * MIB + 77)
+    w, mn, mx = params("mixed_4g_seed1", alg, 8192)
+    exp = oracle.chunk(alg, data, w, mn, mx)
+    ck = Chunker(0)
+    try:
+        d = torch.from_numpy(data).cuda()
+        ck.reserve(alg, w, mn, mx, d.numel())
+        out = torch.full((d.numel() // mn + 2,), -1, dtype=torch.int64, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            ck.chunk_async(d, alg, w, mn, mx, out, cnt, stream=s)
+        for _ in range(2):
+            out.fill_(-1)
+            with torch.cuda.stream(s):
+                g.replay()
+            s.synchronize()
+            ck.sync_status(s)
+            n = int(cnt.item())
+            assert n == exp.size and np.array_equal(out[:n].cpu().numpy().astype(np.uint64), exp), alg
+        assert ck.last_stage() == 2
+    finally:
+        ck.close()
