@@ -228,7 +228,15 @@ CDC_API cdc_status cdc_profile_collect(cdc_handle h, int* calls, double* summary
  * the one-warp-per-chain phase, stitch walks of more than 64 steps,
  * (steps << 32 | segment) of the longest one, the output kernel's passes over
  * step logs, records it replayed, its cycles and the part of them spent in
- * its own chain steps (25 counters).
+ * its own chain steps (25 counters). When the call took the candidate graph
+ * (cdc_last_stage 2) the counters are the graph's instead: segments,
+ * candidates, F evaluated by stepping, the local kernel's cycles summed over
+ * segments (staging, F, pointer jumping), jumping rounds, the longest segment,
+ * the stepped F's cycles and the longest one, the candidate kernel's cycles
+ * summed over chunks (staging, listing blocks, testing their bytes, writing),
+ * blocks listed, the longest segment of each local-kernel phase, (cycles << 24
+ * | segment) of the longest local segment and the longest candidate-kernel
+ * chunk (20 counters).
  * Synchronises `stream`. */
 CDC_API cdc_status cdc_stats(cdc_handle h, uint64_t* out, int n, cdc_stream stream);
 
