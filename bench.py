@@ -73,10 +73,10 @@ def sources_sha(paths) -> str:
     return h.hexdigest()[:16]
 
 
-def profile_traffic():
+def profile_traffic(path: str = None):
     """DRAM bytes per input byte of the speculation kernel from the capture
     record, if that record was taken on the current kernel sources."""
-    p = os.path.join(ROOT, SPEC_TRAFFIC)
+    p = path or os.path.join(ROOT, SPEC_TRAFFIC)
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -179,7 +179,7 @@ def allreduce_max(x: float, world: int) -> float:
     return float(t.item())
 
 
-def write_traffic(csv_path: str, input_bytes: int, command: str):
+def write_traffic(csv_path: str, input_bytes: int, command: str, out_path: str = None):
     """Write SPEC_TRAFFIC from an ncu CSV (metrics dram__bytes_read.sum,
     dram__bytes_write.sum, gpu__time_duration.sum) of k_spec launches that
     each chunked `input_bytes` bytes: DRAM bytes per input byte per launch and
@@ -211,7 +211,7 @@ def write_traffic(csv_path: str, input_bytes: int, command: str):
            "dram_bytes_per_input_byte": sum(x["dram_bytes_per_input_byte"] for x in launches) / len(launches),
            "source_sha256_16": sources_sha(SPEC_SOURCES), "command": command,
            "note": "times under ncu are serialised and cold; only the byte counts are used"}
-    with open(os.path.join(ROOT, SPEC_TRAFFIC), "w") as f:
+    with open(out_path or os.path.join(ROOT, SPEC_TRAFFIC), "w") as f:
         json.dump(rec, f, indent=1)
     print(json.dumps(rec))
 
