@@ -12,10 +12,10 @@
 //              maxima, and against raw bytes only for the two partial blocks
 //              at the window ends.
 //
-// Data movement: persistent CTAs stream 16 KiB tiles from HBM into a ring of
-// shared-memory stages with 1-D bulk copies (cp.async.bulk + mbarrier
-// complete_tx); all threads then read the tile with conflict-free 16-byte
-// shared loads. The kernel is bound by HBM bandwidth: it reads each input
+// Data movement: persistent CTAs stream 16 KiB tiles (MAXP: 32 KiB and a halo
+// on each side) from HBM into a ring of shared-memory stages with 1-D bulk
+// copies (cp.async.bulk + mbarrier complete_tx); all threads then read the
+// tile with conflict-free 16-byte shared loads. The kernel is bound by HBM bandwidth: it reads each input
 // byte once and writes 2 bytes (1 for MAXP) per 64 input bytes.
 #include "cdc_device.cuh"
 #include "cdc_launch.h"
@@ -184,45 +184,54 @@ __global__ void __launch_bounds__(S1_THREADS) k_summary_max(SumLaunch a) {
 
 // ---- MAXP targets --------------------------------------------------------------
 
-// one thread per stage block (the tile's 256 blocks and up to 32 halo blocks)
-// in the block-key pass, so that the halo costs no second round
-constexpr int MP_THREADS = 288;
-constexpr int MP_TILE_BLOCKS = 256;  // 16 KiB of targets per tile
+// Bytes of x in 16-bit lanes plus Kv = (0x8000 - v) * 0x00010001: bit 15 or
+// 31 of either half of the result is set exactly when a byte is >= v
+// (1 <= v <= 255), as b + 0x8000 - v carries into the lane's top bit.
+__device__ __forceinline__ uint32_t ge_lanes(uint32_t x, uint32_t Kv) {
+    return (__byte_perm(x, 0, 0x4240) + Kv) | (__byte_perm(x, 0, 0x4341) + Kv);
+}
 
-// Dynamic shared memory: 2 stages of (MP_TILE_BLOCKS + 2*hb) * 64 bytes, then
-// per-stage-block max / first-position arrays (and one spare), then 2 mbarriers.
-__global__ void __launch_bounds__(MP_THREADS, 5) k_summary_maxp(SumLaunch a) {
+// Tiles of TB blocks (TB * 64 bytes of targets). TH = TB + 32 threads: one per
+// stage block (the tile's blocks and up to 32 halo blocks) in the block-key
+// pass, so that the halo costs no second round.
+//
+// Three barriers per tile: (1) the keys of every stage block are in shared
+// memory, (2) the prefilter has listed its survivors, (3) the survivors'
+// results are in the tile's target mask. The stage is refilled after (3), and
+// every thread then writes its block's result with no further barrier: keys
+// and masks are double-buffered by tile parity, so the next tile's key pass
+// can start while slower warps still write this tile's results.
+//
+// Dynamic shared memory: 2 stages of (TB + 2*hb) * 64 bytes, then per tile
+// parity the stage blocks' maxima and first positions, then 2 mbarriers.
+template <int TB, int TH, int MINB>
+__global__ void __launch_bounds__(TH, MINB) k_summary_maxp(SumLaunch a) {
+    static_assert(TH >= TB + 32 && TB % 64 == 0 && TH % 32 == 0, "one thread per tile block, one halo warp");
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
     const uint32_t hb = a.halo_blocks;
-    const uint32_t nb = MP_TILE_BLOCKS + 2 * hb;  // blocks per stage
+    const uint32_t nb = TB + 2 * hb;  // blocks per stage
     const uint32_t sbytes = nb * 64;
     uint8_t* buf = smem;
-    uint8_t* bm = smem + 2 * sbytes;
-    uint8_t* bf = bm + nb;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + ((2 * sbytes + 3 * nb + 15) & ~15u));
-    __shared__ unsigned int supcnt[MP_TILE_BLOCKS / 64];
-    __shared__ uint16_t qlist[MP_TILE_BLOCKS];  // candidates waiting for a byte test of their end blocks
-    __shared__ uint8_t qres[MP_TILE_BLOCKS];
-    __shared__ unsigned int qn;
-    __shared__ uint16_t slist[MP_TILE_BLOCKS];  // blocks that passed the prefilter
-    __shared__ uint8_t tstate[MP_TILE_BLOCKS];  // 0: no target, 1: target, 2: queued for byte tests
+    uint8_t* bmx = smem + 2 * sbytes;  // [parity][stage block] block maximum
+    uint8_t* bfx = bmx + 2 * nb;       // [parity][stage block] first position of the maximum
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + ((2 * sbytes + 4 * nb + 15) & ~15u));
+    __shared__ uint16_t slist[TB];        // tile blocks that passed the prefilter
+    __shared__ uint32_t okm[2][TB / 32];  // [parity] tile blocks holding a target
     __shared__ unsigned int sn;
     if (blockIdx.x == 0 && tid == 0) reset_ctrl(a.ctrl);
-    const uint64_t ntiles = (a.nblk + MP_TILE_BLOCKS - 1) / MP_TILE_BLOCKS;
+    const uint64_t ntiles = (a.nblk + TB - 1) / TB;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    if (tid < MP_TILE_BLOCKS / 64) supcnt[tid] = 0;
-    if (tid == 0) qn = 0;
     __syncthreads();
     const uint64_t g = gridDim.x;
-    // stage block 0 stands for global block t * MP_TILE_BLOCKS - hb (negative
-    // positions and positions outside [glo, ghi) are not copied)
+    // stage block 0 stands for global block t * TB - hb (negative positions and
+    // positions outside [glo, ghi) are not copied)
     auto issue = [&](uint64_t t, int s) {
-        int64_t r0 = ((int64_t)(t * MP_TILE_BLOCKS) - (int64_t)hb) * 64, r1 = r0 + (int64_t)sbytes;
+        int64_t r0 = ((int64_t)(t * TB) - (int64_t)hb) * 64, r1 = r0 + (int64_t)sbytes;
         int64_t c0 = r0 > (int64_t)a.glo ? r0 : (int64_t)a.glo;
         int64_t c1 = r1 < (int64_t)a.ghi ? r1 : (int64_t)a.ghi;
         uint8_t* dst = buf + s * sbytes;
@@ -241,11 +250,10 @@ __global__ void __launch_bounds__(MP_THREADS, 5) k_summary_maxp(SumLaunch a) {
         }
     }
     const uint32_t w = a.w;
-    // blocks this close to a block lie inside the window of any byte of it
-    const uint32_t K = w >= 63 ? (w - 63) / 64 : 0;
+    const uint32_t li = (uint32_t)tid & 7u;
     uint32_t i = 0;
     for (uint64_t t = blockIdx.x; t < ntiles; t += g, i++) {
-        const int s = i & 1;
+        const int s = i & 1;  // stage, and parity of the key and mask buffers
         const uint32_t par = (i >> 1) & 1u;
         if (!mbar_wait_bounded(&bar[s], par, a.timeout_ns)) {
             atomicOr(&a.ctrl->err, ERR_TIMEOUT);
@@ -254,9 +262,14 @@ __global__ void __launch_bounds__(MP_THREADS, 5) k_summary_maxp(SumLaunch a) {
             return;
         }
         const uint8_t* tb = buf + s * sbytes;
-        const int64_t sb0 = (int64_t)(t * MP_TILE_BLOCKS) - (int64_t)hb;  // global block of stage block 0
-        // 1) block max and first position of the max, for every stage block
-        for (uint32_t sb = tid; sb < nb; sb += MP_THREADS) {
+        uint8_t* bm = bmx + s * nb;
+        uint8_t* bf = bfx + s * nb;
+        uint32_t* okw = okm[s];
+        const int64_t sb0 = (int64_t)(t * TB) - (int64_t)hb;  // global block of stage block 0
+        // 1) block max and first position of the max, for every stage block.
+        // (The buffers of this parity were last read by tile i-2, which every
+        // thread finished before barrier (1) of tile i-1.)
+        for (uint32_t sb = tid; sb < nb; sb += TH) {
             const int64_t gblk = sb0 + (int64_t)sb;
             uint32_t kf = 255u;  // blocks before position 0: max 0, first position 0
             if (gblk >= 0) {
@@ -268,115 +281,93 @@ __global__ void __launch_bounds__(MP_THREADS, 5) k_summary_maxp(SumLaunch a) {
             bf[sb] = (uint8_t)(255u - (kf & 0xFFu));
         }
         if (tid == 0) sn = 0;
-        __syncthreads();
-        // 2) prefilter, one thread per tile block: the blocks within K of it lie
-        // inside the window wherever the maximum sits in its block, so none of
-        // them may reach its maximum. Survivors (a small share) are listed.
-        static_assert(MP_THREADS >= MP_TILE_BLOCKS && MP_THREADS % 32 == 0, "one tile block per thread");
-        if (tid < MP_TILE_BLOCKS) {
+        if (tid < TB / 32) okw[tid] = 0;
+        __syncthreads();  // (1)
+        // 2) prefilter, one thread per tile block: every block strictly inside
+        // the maximum's window must stay below the maximum. Survivors (a small
+        // share) are listed.
+        if (tid < TB) {
             const uint32_t lb = (uint32_t)tid;
-            const uint64_t gb = t * MP_TILE_BLOCKS + lb;
             const uint32_t sbi = hb + lb;
             const uint32_t v = bm[sbi];
-            bool pass = gb < a.nblk && v != 0;
-            for (uint32_t k = 1; k <= K && pass; k++)
-                if (bm[sbi - k] >= v || bm[sbi + k] >= v) pass = false;
-            tstate[lb] = 0;
+            const uint32_t P = 64 * sbi + bf[sbi];  // the maximum's offset in the stage (> w)
+            // interior blocks on each side (-1: the window ends inside the block)
+            const int rl = (int)sbi - (int)((P - w) >> 6) - 1, rr = (int)((P + w) >> 6) - (int)sbi - 1;
+            // both windows inside the data (checked here, while most blocks are
+            // still candidates, to keep the survivors few)
+            const uint64_t p = (t * TB + lb) * 64 + bf[sbi];
+            bool pass = t * TB + lb < a.nblk && v != 0 && p >= a.lo + w && p + w < a.hi;
+            // nearest blocks first; most blocks fail at once
+            for (int d = 1; pass && (d <= rl || d <= rr); d++)
+                pass = (d > rl || bm[sbi - d] < v) && (d > rr || bm[sbi + d] < v);
             if (pass) slist[atomicAdd(&sn, 1u)] = (uint16_t)lb;
         }
-        __syncthreads();
-        // 3) survivors: a unique maximum (its last position equals its first),
-        // both windows inside the data, the remaining interior blocks of the
-        // window below it; a survivor whose partial end blocks may hold a byte
-        // >= its value is queued, and whole warps test those bytes (16 lanes
-        // per end block).
-        for (uint32_t k = tid; k < sn; k += MP_THREADS) {
-            const uint32_t lb = slist[k];
-            const uint64_t gb = t * MP_TILE_BLOCKS + lb;
-            const uint32_t sbi = hb + lb;
-            const uint64_t P0 = gb * 64;
-            const bool edge = P0 < a.lo || P0 + 64 > a.hi;
-            const uint32_t kl = block_key<true>(tb + 64 * sbi, (sbi >> 1) & 3u, 0u, edge, P0, a.lo, a.hi);
-            const uint32_t v = bm[sbi];
-            const uint64_t p = P0 + bf[sbi];
-            uint32_t state = 0;  // 0: no target, 1: target, 2: queued
-            if (bf[sbi] == (kl & 0xFFu) && p >= a.lo + w && p + w < a.hi) {
-                const uint64_t wl = p - w, wr = p + w;  // window [wl, wr]
-                const uint32_t s0 = (uint32_t)((int64_t)(wl >> 6) - sb0), s1 = (uint32_t)((int64_t)(wr >> 6) - sb0);
-                bool ok = true;
-                for (uint32_t si = s0 + 1; si < sbi - K && ok; si++)
-                    if (bm[si] >= v) ok = false;
-                for (uint32_t si = sbi + K + 1; si < s1 && ok; si++)
-                    if (bm[si] >= v) ok = false;
-                bool queue = false;
-                if (ok && s0 != sbi && bm[s0] >= v) {
-                    if ((wl & 63) == 0) ok = false;  // the whole block lies in the window
-                    else queue = true;
-                }
-                if (ok && s1 != sbi && s1 != s0 && bm[s1] >= v) {
-                    if ((wr & 63) == 63) ok = false;
-                    else queue = true;
-                }
-                state = ok ? (queue ? 2u : 1u) : 0u;
-            }
-            tstate[lb] = (uint8_t)state;
-            if (state == 2) qlist[atomicAdd(&qn, 1u)] = (uint16_t)lb;
-        }
-        __syncthreads();
-        for (uint32_t q = (uint32_t)(tid >> 5); q < qn; q += MP_THREADS / 32) {
-            const int lane = tid & 31;
-            const uint32_t lb = qlist[q];
-            const uint64_t gb = t * MP_TILE_BLOCKS + lb;
-            const uint32_t sbi = hb + lb;
-            const uint32_t v = bm[sbi];
-            const uint64_t p = gb * 64 + bf[sbi], wl = p - w, wr = p + w;
-            const uint32_t s0 = (uint32_t)((int64_t)(wl >> 6) - sb0), s1 = (uint32_t)((int64_t)(wr >> 6) - sb0);
-            // lanes 0..15: words of the left end block from wl on; 16..31: right end block up to wr
-            const bool left = lane < 16;
-            const uint32_t si = left ? s0 : s1;
-            const bool need = si != sbi && (left || s1 != s0) && bm[si] >= v;
-            uint32_t f = 0;
-            if (need) {
-                const uint32_t j = (uint32_t)(lane & 15);
-                const uint32_t o0 = left ? (uint32_t)(wl & 63) : 0u, o1 = left ? 63u : (uint32_t)(wr & 63);
-                uint32_t x = *reinterpret_cast<const uint32_t*>(tb + (size_t)si * 64 + 4 * j);
-                if (4 * j + 3 < o0 || 4 * j > o1) x = 0;
-                if (4 * j < o0 && 4 * j + 3 >= o0) x &= 0xFFFFFFFFu << (8 * (o0 - 4 * j));
-                if (4 * j <= o1 && 4 * j + 3 > o1) x &= 0xFFFFFFFFu >> (8 * (4 * j + 3 - o1));
+        __syncthreads();  // (2)
+        // 3) survivors, eight lanes each (lane li holds bytes 8li..8li+7 of a
+        // block): no byte of the own block but the maximum, nor any byte of the
+        // two partial end blocks that lies in the window, may reach the maximum.
+        // Every warp runs the same number of rounds (the ballot takes whole warps).
+        const uint32_t nsv = sn;
+        for (uint32_t k0 = 0; k0 < nsv; k0 += TH / 8) {
+            const uint32_t k = k0 + ((uint32_t)tid >> 3);
+            const bool act = k < nsv;
+            uint32_t lb = 0, hit = 0;
+            if (act) {
+                lb = slist[k];
+                const uint32_t sbi = hb + lb;
+                const uint32_t v = bm[sbi], f = bf[sbi];
+                const uint64_t p = (t * TB + lb) * 64 + f;  // both windows inside the data (prefilter)
+                const uint32_t o0 = (uint32_t)((p - w) & 63), o1 = (uint32_t)((p + w) & 63);
+                const uint32_t s0 = (uint32_t)((int64_t)((p - w) >> 6) - sb0);
+                const uint32_t s1 = (uint32_t)((int64_t)((p + w) >> 6) - sb0);
                 const uint32_t Kv = (0x8000u - v) * 0x00010001u;
-                const uint32_t e = __byte_perm(x, 0, 0x4240), o = __byte_perm(x, 0, 0x4341);
-                f = ((e + Kv) | (o + Kv)) & 0x80008000u;
+                const int b8 = 64 * (int)li;  // bit offset of the lane's first byte
+                {
+                    const uint2 q = *reinterpret_cast<const uint2*>(tb + 64 * sbi + 8 * li);
+                    const uint32_t d = f - 8 * li;  // the maximum's byte among the lane's eight, if < 8
+                    const uint32_t x0 = d < 4 ? q.x & ~(0xFFu << (8 * d)) : q.x;
+                    const uint32_t x1 = (d - 4) < 4 ? q.y & ~(0xFFu << (8 * (d - 4))) : q.y;
+                    hit |= ge_lanes(x0, Kv) | ge_lanes(x1, Kv);
+                }
+                if (s0 != sbi && bm[s0] >= v) {  // left end block: offsets >= o0
+                    const uint2 q = *reinterpret_cast<const uint2*>(tb + 64 * s0 + 8 * li);
+                    const int d = 8 * (int)o0 - b8;
+                    const uint32_t x0 = q.x & __funnelshift_lc(0u, 0xFFFFFFFFu, (uint32_t)min(max(d, 0), 32));
+                    const uint32_t x1 = q.y & __funnelshift_lc(0u, 0xFFFFFFFFu, (uint32_t)min(max(d - 32, 0), 32));
+                    hit |= ge_lanes(x0, Kv) | ge_lanes(x1, Kv);
+                }
+                if (s1 != sbi && bm[s1] >= v) {  // right end block: offsets <= o1
+                    const uint2 q = *reinterpret_cast<const uint2*>(tb + 64 * s1 + 8 * li);
+                    const int d = b8 + 24 - 8 * (int)o1;
+                    const uint32_t x0 = q.x & __funnelshift_rc(0xFFFFFFFFu, 0u, (uint32_t)min(max(d, 0), 32));
+                    const uint32_t x1 = q.y & __funnelshift_rc(0xFFFFFFFFu, 0u, (uint32_t)min(max(d + 32, 0), 32));
+                    hit |= ge_lanes(x0, Kv) | ge_lanes(x1, Kv);
+                }
             }
-            const uint32_t bal = __ballot_sync(FULL, f != 0);
-            if (lane == 0) qres[lb] = bal == 0 ? 1 : 0;
+            const uint32_t bal = __ballot_sync(FULL, (hit & 0x80008000u) != 0);
+            if (act && li == 0 && ((bal >> (tid & 24)) & 0xFFu) == 0) atomicOr(&okw[lb >> 5], 1u << (lb & 31));
         }
-        __syncthreads();
-        // the stage's bytes are no longer read: refill it with the tile after next
-        if (tid == 0) {
+        __syncthreads();  // (3)
+        // the stage's bytes are no longer read: refill it with the tile after
+        // next (from the halo warp, which has no result to write)
+        if (tid == TH - 32) {
             uint64_t tn = t + 2 * g;
             if (tn < ntiles) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 issue(tn, s);
             }
         }
-        if (tid < MP_TILE_BLOCKS) {  // (whole warps)
+        // 4) results: the target's offset or 0xFF per block, and the targets
+        // per 4 KiB superblock (64 blocks: two mask words)
+        if (tid < TB) {
             const uint32_t lb = (uint32_t)tid;
-            const uint64_t gb = t * MP_TILE_BLOCKS + lb;
-            const uint32_t state = tstate[lb];
-            const bool ok = state == 1 || (state == 2 && qres[lb]);
-            if (gb < a.nblk) a.smax[gb] = ok ? bf[hb + lb] : (uint8_t)0xFFu;
-            // targets per 4 KiB superblock (64 blocks = 2 warps)
-            const uint32_t cntw = __popc(__ballot_sync(FULL, ok));
-            if ((tid & 31) == 0 && cntw) atomicAdd(&supcnt[lb >> 6], cntw);
-            if (tid == 0) qn = 0;
+            const uint64_t gb = t * TB + lb;
+            if (gb < a.nblk) a.smax[gb] = ((okw[lb >> 5] >> (lb & 31)) & 1u) ? bf[hb + lb] : (uint8_t)0xFFu;
         }
-        __syncthreads();
-        if (tid < MP_TILE_BLOCKS / 64) {
-            uint64_t q = t * (MP_TILE_BLOCKS / 64) + tid;
-            if (q < a.nsup) a.ssup[q] = (uint8_t)min(supcnt[tid], 255u);
-            supcnt[tid] = 0;
+        if (tid < TB / 64) {
+            const uint64_t q = t * (TB / 64) + tid;
+            if (q < a.nsup) a.ssup[q] = (uint8_t)(__popc(okw[2 * tid]) + __popc(okw[2 * tid + 1]));
         }
-        __syncthreads();
     }
 }
 
@@ -384,15 +375,19 @@ __global__ void __launch_bounds__(MP_THREADS, 5) k_summary_maxp(SumLaunch a) {
 
 int summary_max_smem() { return S1_STAGES * S1_TILE + S1_STAGES * 8; }
 
+// MAXP tiles: 512 blocks (32 KiB), 544 threads, 3 CTAs per SM (32 registers)
+constexpr int MP_TILE_BLOCKS = 512, MP_THREADS = 544, MP_MIN_CTAS = 3;
+static constexpr auto maxp_kernel = k_summary_maxp<MP_TILE_BLOCKS, MP_THREADS, MP_MIN_CTAS>;
+
 int summary_maxp_smem(uint32_t halo_blocks) {
     uint32_t nb = MP_TILE_BLOCKS + 2 * halo_blocks;
-    return (int)(((2 * nb * 64 + 3 * nb + 15) & ~15u) + 16);
+    return (int)(((2 * nb * 64 + 4 * nb + 15) & ~15u) + 16);
 }
 
 uint32_t maxp_halo_blocks(uint32_t w) { return (w + 63) / 64 + 1; }
 
 static int allow_summary_smem(int kind) {
-    if (kind == SUM_MAXP) return launch_memo(300, 0, [](uint32_t) { return allow_max_smem(k_summary_maxp); });
+    if (kind == SUM_MAXP) return launch_memo(300, 0, [](uint32_t) { return allow_max_smem(maxp_kernel); });
     if (kind == SUM_MAX_INV) return launch_memo(301, 0, [](uint32_t) { return allow_max_smem(k_summary_max<true>); });
     return launch_memo(302, 0, [](uint32_t) { return allow_max_smem(k_summary_max<false>); });
 }
@@ -401,7 +396,7 @@ cudaError_t launch_summary(const SumLaunch& a, int kind, int grid, cudaStream_t 
     const int set = allow_summary_smem(kind);
     if (set != (int)cudaSuccess) return (cudaError_t)set;
     if (kind == SUM_MAXP) {
-        k_summary_maxp<<<grid, MP_THREADS, summary_maxp_smem(a.halo_blocks), st>>>(a);
+        maxp_kernel<<<grid, MP_THREADS, summary_maxp_smem(a.halo_blocks), st>>>(a);
     } else if (kind == SUM_MAX_INV) {
         k_summary_max<true><<<grid, S1_THREADS, summary_max_smem(), st>>>(a);
     } else {
@@ -420,7 +415,7 @@ int summary_blocks_per_sm(int kind, uint32_t halo_blocks) {
     if (kind == SUM_MAXP)
         return launch_memo(310, halo_blocks, [](uint32_t hb) {
             int n = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_summary_maxp, MP_THREADS, summary_maxp_smem(hb));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, maxp_kernel, MP_THREADS, summary_maxp_smem(hb));
             return n > 0 ? n : 1;
         });
     return launch_memo(311, 0, [](uint32_t) {
