@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(TH, MINB) k_summary_maxp(SumLaunch a) {
         }
     }
     const uint32_t w = a.w;
+    const uint32_t K = (w - 63) / 64;  // w >= 63
     const uint32_t li = (uint32_t)tid & 7u;
     uint32_t i = 0;
     for (uint64_t t = blockIdx.x; t < ntiles; t += g, i++) {
@@ -297,8 +298,13 @@ __global__ void __launch_bounds__(TH, MINB) k_summary_maxp(SumLaunch a) {
             // still candidates, to keep the survivors few)
             const uint64_t p = (t * TB + lb) * 64 + bf[sbi];
             bool pass = t * TB + lb < a.nblk && v != 0 && p >= a.lo + w && p + w < a.hi;
-            // nearest blocks first; most blocks fail at once
-            for (int d = 1; pass && (d <= rl || d <= rr); d++)
+            // the K nearest blocks on each side lie inside the window wherever
+            // the maximum sits: independent loads, no early exit
+            uint32_t nm = 0;
+            for (int d = 1; d <= (int)K; d++) nm = max(nm, max((uint32_t)bm[sbi - d], (uint32_t)bm[sbi + d]));
+            pass = pass && nm < v;
+            // then the (at most one) remaining interior block on each side
+            for (int d = (int)K + 1; pass && (d <= rl || d <= rr); d++)
                 pass = (d > rl || bm[sbi - d] < v) && (d > rr || bm[sbi + d] < v);
             if (pass) slist[atomicAdd(&sn, 1u)] = (uint16_t)lb;
         }
