@@ -260,3 +260,34 @@ def test_host_entry_point(ck):
         w, mn, mx = params("mixed_4g_seed1", alg, 4096)
         got = ck.chunk_host(data, alg, w, mn, mx)
         assert np.array_equal(got, oracle.chunk(alg, data, w, mn, mx)), alg
+
+
+@pytest.mark.parametrize("w", [63, 64, 127, 128, 1000, 2111, 4095, 16384])
+def test_maxp_window_sizes(ck, w):
+    """MAXP over the window sizes its block-summary kernel takes (63 to 16384 bytes):
+    halos of 2 to 258 blocks each side, one or two rounds of the block-key pass."""
+    rng = np.random.default_rng(w)
+    n = 8 * MIB
+    data = (synth.uniform(5, n) >> 1).astype(np.uint8)  # background below 128
+    spikes = rng.integers(0, n, size=max(4, n // max(w // 2, 1)))  # about two per window
+    data[spikes] = rng.integers(128, 256, size=spikes.size).astype(np.uint8)
+    expect_equal(ck, data, "maxp", w, 64, max(8 * w, 65536), tag="window")
+
+
+def test_maxp_maxima_at_block_edges(ck):
+    """Isolated maxima on the first or the last byte of 64-byte blocks, where with
+    w = 63 a window ends inside the maximum's own block, and spikes that tie with
+    their neighbour (no target on either side)."""
+    rng = np.random.default_rng(11)
+    n = 2 * MIB
+    data = np.zeros(n, dtype=np.uint8)
+    pos = np.cumsum(rng.integers(60, 400, size=n // 60))
+    pos = pos[pos < n - 64]
+    pos = (pos & ~63) + np.where(rng.random(pos.size) < 0.5, 0, 63)
+    pos = np.unique(pos)
+    val = rng.integers(1, 256, size=pos.size).astype(np.uint8)
+    tie = rng.random(pos.size) < 0.2
+    val[1:][tie[1:]] = val[:-1][tie[1:]]
+    data[pos] = val
+    for w in (63, 64, 100, 191):
+        expect_equal(ck, data, "maxp", w, 1, 1 << 16, tag="block-edges")
