@@ -949,6 +949,14 @@ def main():
     iso_achieved = n / (iso_spec_ms / 1e3) / 1e9
     iso_sum_ms = sum(r["summary_ms"] for r in iso) / max(1, len(iso))
     sum_achieved = n / (iso_sum_ms / 1e3) / 1e9
+    # the two summary kernels apart: RAM/AE (maxima) and MAXP (targets)
+    sum_kernels = {}
+    for kn, algs in (("k_summary_max", ("ram", "ae")), ("k_summary_maxp", ("maxp",))):
+        rows = [r["summary_ms"] for r in iso if r["alg"] in algs and r["summary_ms"] > 0]
+        if rows:
+            kms = sum(rows) / len(rows)
+            sum_kernels[kn] = {"achieved": round(n / (kms / 1e3) / 1e9, 1),
+                               "frac": round(n / (kms / 1e3) / 1e9 / peak, 4), "avg_launch_ms": round(kms, 4)}
     # which chain stage the calls took (the automatic policy: the candidate
     # graph up to 512 MiB, 768 MiB for AE; speculation beyond)
     stages = sorted({ck.last_stage() for ck in handles})
@@ -969,7 +977,7 @@ def main():
                                  "note": "the step's nine calls overlap on %d streams" % nstreams},
                 "summary_kernel": {"kernel": "k_summary_max / k_summary_maxp (block summaries: reads every byte)",
                                    "achieved": round(sum_achieved, 1), "frac": round(sum_achieved / peak, 4),
-                                   "avg_launch_ms": round(iso_sum_ms, 4)}}
+                                   "avg_launch_ms": round(iso_sum_ms, 4), "per_kernel": sum_kernels}}
     line = {"metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded)",
