@@ -304,8 +304,10 @@ __global__ void __launch_bounds__(TH, MINB) k_summary_maxp(SumLaunch a) {
             for (int d = 1; d <= (int)K; d++) nm = max(nm, max((uint32_t)bm[sbi - d], (uint32_t)bm[sbi + d]));
             pass = pass && nm < v;
             // then the (at most one) remaining interior block on each side
-            for (int d = (int)K + 1; pass && (d <= rl || d <= rr); d++)
-                pass = (d > rl || bm[sbi - d] < v) && (d > rr || bm[sbi + d] < v);
+            const int d1 = (int)K + 1;
+            if (d1 <= rl) nm = max(nm, (uint32_t)bm[sbi - d1]);
+            if (d1 <= rr) nm = max(nm, (uint32_t)bm[sbi + d1]);
+            pass = pass && nm < v;
             if (pass) slist[atomicAdd(&sn, 1u)] = (uint16_t)lb;
         }
         __syncthreads();  // (2)
